@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Throughput of the swept-source holographic OCT reconstruction on GB300.
+
+One step = one whole reconstruction of a 1024 x 1024 x 256 volume from uint16
+frames already resident in HBM: chromatic rescale (Eq. 5) + Fresnel transform
+(Eq. 6) of all 256 frames, sweep-axis transform (Eq. 7), |V|^2 volume, and the
+three orthogonal cuts.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ssoct|reference]
+
+--impl reference times the FP64 CPU oracle on this host's cores on a bounded
+sample of the same workload.  Under torchrun (N > 1) each rank reconstructs its
+own volumes (replicas: the path has no exchange step between volumes).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gvoxel/s, 1024²×256 volume recon, FP32 vs tensor-core form; % of HBM roofline"
+UNIT = "Gvoxel/s"
+WORKLOAD = "paper_1024x1024x256"
+PAPER_GVOXEL_PER_S = 10.0   # TITAN Xp, Table 1 of the paper (context only)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms while running."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + f[0].split(".")[1]) if "." in f[0] else 0.0
+                rows.append((ts, float(f[2]), float(f[3]), f[5:]))
+            except (ValueError, IndexError):
+                continue
+        if not rows:
+            return None
+        inside = [r for r in rows if self.t0 - 0.05 <= r[0] <= self.t1 + 0.05] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for n, v in zip(names, r[3][1:]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_rate(w, n_frames: int):
+    """FP64 oracle (as it stands) on a gate of the first n_frames frames of the
+    workload: returns (voxels per second, seconds, threads)."""
+    import oracle
+    t = time.perf_counter()
+    oracle.reconstruct(w.frames[:n_frames], w.pitch, w.z, w.lambdas[:n_frames], method="fft")
+    dt = time.perf_counter() - t
+    return w.nx * w.ny * n_frames / dt, dt, os.cpu_count()
+
+
+def _sample_frames(w, budget_s: float) -> int:
+    rate, dt, _ = oracle_rate(w, 2)
+    per_frame = dt / 2.0
+    return int(max(2, min(w.nlambda, budget_s / per_frame)))
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    import synth
+    w = synth.workload(WORKLOAD)
+    budget = max(0.5, 150.0 / (args.steps + args.warmup))
+    n = _sample_frames(w, budget)
+    for _ in range(args.warmup):
+        oracle_rate(w, n)
+    times = []
+    for _ in range(args.steps):
+        _, dt, cores = oracle_rate(w, n)
+        times.append(dt)
+    total = sum(times)
+    vox = w.nx * w.ny * n
+    value = vox * args.steps / total / 1e9
+    sample = (f"oracle.reconstruct (float64 numpy/scipy.fft) of a {w.nx}x{w.ny}x{n} gate: the first {n} "
+              f"frames of the {w.nx}x{w.ny}x{w.nlambda} workload, per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_GVOXEL_PER_S,
+        "dtype": "f64", "data": "synthetic (seeded point scatterers, 12-bit, Gaussian read noise)",
+        "config": {"workload": f"{w.nx}x{w.ny}x{w.nlambda} sweep, FP64 CPU oracle on a {n}-frame sample",
+                   "window": [0, 0, w.nx, w.ny]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ssoct(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2003_08960_gb300 as ss
+    import synth
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = synth.workload(WORKLOAD, seed=3 + rank)
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    h = plan.handle
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    frames = torch.from_numpy(w.frames.view(np.int16)).cuda()
+    vol, _ = plan.empty_volume()
+    nl, wy, wx = plan.volume_shape()
+    xy = torch.empty((wy, wx), dtype=torch.float32, device="cuda")
+    xz = torch.empty((nl, wx), dtype=torch.float32, device="cuda")
+    yz = torch.empty((nl, wy), dtype=torch.float32, device="cuda")
+    cut = (wx // 2 + wx // 4, wy // 2 + wy // 4, nl // 2)
+    torch.cuda.synchronize()
+
+    def step():
+        st = ss.ssoct_reconstruct_frames(h, frames.data_ptr(), vol.data_ptr(), 0, sp)
+        st |= ss.ssoct_get_cuts(h, vol.data_ptr(), cut[0], cut[1], cut[2], xy.data_ptr(), xz.data_ptr(),
+                                yz.data_ptr(), sp)
+        if st:
+            raise RuntimeError(ss.ssoct_last_error(h))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    if ss.ssoct_sync(h, sp) != 0:
+        raise RuntimeError(ss.ssoct_last_error(h))
+    ss.ssoct_profile(h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark(False)
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = ss.ssoct_sync(h, sp)
+    if st != 0:
+        raise RuntimeError("kernel error: " + ss.ssoct_last_error(h))
+    _, lat_ms, ax_ms, calls = ss.ssoct_profile_read(h)
+    ss.ssoct_profile(h, False)
+    clk = clocks.stop()
+    lat_ms /= max(calls, 1)
+    ax_ms /= max(calls, 1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    voxels = wx * wy * nl
+    value = world * voxels / (ms * 1e-3) / 1e9
+
+    # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
+    host_frames = torch.from_numpy(w.frames.view(np.int16)).pin_memory()
+    host_vol = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        s1 = ss.ssoct_push_frames(h, host_frames.data_ptr(), nl, False, -1, sp)
+        s2 = ss.ssoct_reconstruct_volume(h, vol.data_ptr(), 0, sp)
+        if s1 or s2:
+            raise RuntimeError(ss.ssoct_last_error(h))
+        with torch.cuda.stream(stream):
+            host_vol.copy_(vol, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * voxels / (e2e_ms * 1e-3) / 1e9
+
+    peak, peak_kind = _peaks()
+    lat_bytes = w.nx * w.ny * nl * 2 + voxels * 8
+    ax_bytes = voxels * (8 + 4)
+    kernels = {
+        "lateral": {"ms": lat_ms, "bytes": lat_bytes, "GBps": lat_bytes / (lat_ms * 1e-3) / 1e9},
+        "axial": {"ms": ax_ms, "bytes": ax_bytes, "GBps": ax_bytes / (ax_ms * 1e-3) / 1e9},
+    }
+    for k in kernels.values():
+        k["frac"] = k["GBps"] / peak
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    traffic = _traffic(dom)
+    whole_bytes = lat_bytes + ax_bytes
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_GVOXEL_PER_S, "dtype": "f32",
+        "data": "synthetic (seeded point scatterers, 12-bit, Gaussian read noise)",
+        "config": {"workload": f"{w.nx}x{w.ny}x{nl} sweep, uint16 frames resident in HBM, full window, "
+                               "|V|^2 volume + 3 cuts per step",
+                   "window": [0, 0, wx, wy], "form": "fp32 (paper order)",
+                   "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["GBps"], "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
+                     "traffic": traffic},
+        "whole_step_hbm": {"bytes_per_voxel": whole_bytes / voxels,
+                           "GBps": whole_bytes / (ms * 1e-3) / 1e9,
+                           "frac": whole_bytes / (ms * 1e-3) / 1e9 / peak},
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_frames.numel() * 2),
+                "d2h_bytes_per_step": int(host_vol.numel() * 4), "ms_per_step": e2e_ms},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = _sample_frames(w, 15.0)
+        rate, dt, cores = oracle_rate(w, n)
+        out["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"FP64 oracle on the first {n} frames ({w.nx}x{w.ny}x{n} gate), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel source (null otherwise)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2003_08960_gb300", "csrc", d["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["bytes_per_launch"] if h == d["source_sha256_16"] else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ssoct", choices=["ssoct", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ssoct(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * ssoct.h - C ABI of libssoct, a single-GPU (sm_103a) implementation of the
+ * reconstruction chain of swept-source OCT by off-axis Fresnel-transform digital
+ * holography (Charpentier et al., arXiv:2003.08960):
+ *
+ *   uint16 interferograms I(x, y, t), one per wavelength of a sweep
+ *     -> chromatic rescale I'(x, y, t) = I(x lambda_t/lambda_1, y lambda_t/lambda_1, t)   (Eq. 5)
+ *     -> discrete Fresnel transform with lambda_1, k_1 for every frame            (Eq. 6)
+ *     -> crop to an off-axis window of the hologram plane
+ *     -> transform over the sweep (rectangular gate of N_lambda frames)           (Eq. 7)
+ *     -> |.|^2 volume and three orthogonal cuts (text after Eq. 7, Fig. 5)
+ *
+ * Conventions shared by every call
+ * - All device pointers are CUDA device memory of the current device, owned by
+ *   the caller.  Host pointers are ordinary (pinned or pageable) host memory.
+ * - Calls that take a `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *   default stream) only enqueue work on it and return; results are ready when
+ *   the stream reaches that point.  Statuses are return values; nothing throws.
+ * - Layouts are C order.  A frame is uint16 [ny][nx] (x fastest); a stack is
+ *   [n][ny][nx].  Volumes are [nlambda][wy][wx] (x fastest) with the depth bin q
+ *   unshifted (q = 0 .. nlambda-1).
+ * - A plan is not thread-safe; use one plan per host thread or serialise.
+ * - lambda_1 is lambda_m[0], the wavelength of the first frame of the sweep
+ *   (Eq. 5 and Eq. 6 use it for every frame).
+ */
+#ifndef SSOCT_H
+#define SSOCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SSOCT_API __attribute__((visibility("default")))
+#else
+#define SSOCT_API
+#endif
+
+typedef struct ssoct_plan_s* ssoct_plan;
+
+/* Off-axis window in hologram-plane pixels: columns x0 .. x0+wx-1, rows
+ * y0 .. y0+wy-1 of the Nx x Ny hologram computed by Eq. 6.  {0, 0, nx, ny} is
+ * the whole plane. */
+typedef struct {
+  int x0, y0, wx, wy;
+} ssoct_window;
+
+typedef enum {
+  SSOCT_OK = 0,
+  SSOCT_EINVAL = 1,       /* bad argument: size, pointer, alignment, window, index */
+  SSOCT_ENOMEM = 2,       /* workspace missing or too small */
+  SSOCT_ECUDA = 3,        /* a CUDA runtime call failed (see ssoct_last_error) */
+  SSOCT_EAGAIN = 4,       /* reserved */
+  SSOCT_ENOTREADY = 5,    /* fewer than nlambda frames pushed since the gate (re)started */
+  SSOCT_EDROPPED = 6,     /* a frame sequence number skipped; the gate restarted */
+  SSOCT_ETIMEOUT = 7,     /* a kernel gave up waiting on its own work queue */
+  SSOCT_EUNSUPPORTED = 8  /* valid request outside the sizes this build compiles */
+} ssoct_status;
+
+/* Plan flags. */
+#define SSOCT_FLAG_MAGNITUDE 0x1u /* volume holds |V| instead of |V|^2 */
+
+/* Read-only facts about a plan. */
+typedef struct {
+  int nx, ny, nlambda;
+  ssoct_window window;
+  double lambda1_m;       /* lambda_1 = lambda_m[0] */
+  double dprime_x_m;      /* reconstructed pixel lambda_1 z / (Nx d), Eq. 4 */
+  double dprime_y_m;      /* lambda_1 z / (Ny d) */
+  double z_b_m;           /* max(Nx, Ny) d^2 / lambda_1: Eq. 6 is meant for z >= z_b (text under Eq. 6) */
+  int aliased_chirp;      /* 1 if z < z_b: the input chirp aliases at the frame edge (result still defined) */
+  double prefactor_re;    /* K = (i / (lambda_1 z)) exp(-i k_1 z) d^2, the constant of Eq. 6 */
+  double prefactor_im;
+  size_t workspace_bytes; /* device bytes ssoct_set_workspace needs */
+  int ring_slots;         /* frames of lateral scratch kept (L2-resident) */
+} ssoct_plan_info_t;
+
+/* Create a plan.  Host only: no CUDA call is made here.
+ *   nx, ny     frame size (pixels).  This build compiles nx, ny in {64, 128,
+ *              256, 512, 1024} (square), plus (128, 64) and (64, 128).
+ *   nlambda    frames per sweep = depth bins, N_z of Eq. 3 / the gate of Eq. 7.
+ *              This build compiles {16, 32, 64, 128, 256, 512}.
+ *   pitch_m    camera pixel pitch d > 0.
+ *   z_m        sensor-to-object distance z != 0 of Eq. 6.
+ *   lambda_m   [nlambda] wavelength of each frame of the sweep, > 0; copied.
+ *   win        window (NULL = whole plane); must lie inside the frame.
+ *   flags      SSOCT_FLAG_*.
+ *   out        receives the plan; *out = NULL on error.
+ * Builds in float64 and rounds once to float32: per-frame separable linear-
+ * interpolation taps (Eq. 5, origin at pixel N/2, taps outside the frame read
+ * 0), separable input/output chirps with the centring phase folded in (Eq. 6),
+ * FFT twiddles.  EINVAL / EUNSUPPORTED on bad or uncompiled sizes. */
+SSOCT_API ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, double z_m,
+                                         const double* lambda_m, const ssoct_window* win,
+                                         unsigned flags, ssoct_plan* out);
+
+/* Fill *info.  EINVAL on NULL. */
+SSOCT_API ssoct_status ssoct_plan_info(ssoct_plan plan, ssoct_plan_info_t* info);
+
+/* Device workspace size in bytes (tables, frame ring, L2 scratch ring,
+ * sweep-axis intermediate, counters). */
+SSOCT_API ssoct_status ssoct_workspace_size(ssoct_plan plan, size_t* bytes);
+
+/* Hand the plan caller-owned device memory of at least ssoct_workspace_size
+ * bytes, 256-byte aligned.  Uploads the tables (synchronous copy) on the
+ * current device, which the plan then uses for every call.  ENOMEM if too
+ * small, EINVAL if misaligned or NULL.  The memory must outlive the plan's use. */
+SSOCT_API ssoct_status ssoct_set_workspace(ssoct_plan plan, void* dev_ptr, size_t bytes);
+
+/* Append n frames [n][ny][nx] to the plan's ring of nlambda frames (the
+ * buffered acquisition of the paper's pipeline).  frames_on_device != 0: the
+ * pointer is device memory; otherwise host memory.  Copies are enqueued on
+ * `stream` (one cudaMemcpyAsync per contiguous piece).  first_seq >= 0 is the
+ * camera sequence number of frames[0]: if it is not the number that follows the
+ * previous push, the frames are still stored but the gate restarts with them and
+ * EDROPPED is returned, so that no volume mixes frames across a drop (the paper
+ * buffers acquisition "to avoid any image drop" for a consistent Eq. 7).
+ * first_seq < 0 disables the check.  The frames of a gate must be pushed in
+ * sweep order starting at the sweep's first wavelength. */
+SSOCT_API ssoct_status ssoct_push_frames(ssoct_plan plan, const uint16_t* frames, int n,
+                                         int frames_on_device, int64_t first_seq, void* stream);
+
+/* Reconstruct the volume from the last nlambda pushed frames (ENOTREADY if
+ * fewer).  vol_dev: float32 [nlambda][wy][wx] receives |V|^2 (or |V| with
+ * SSOCT_FLAG_MAGNITUDE), V being Eq. 7 applied to the windowed Eq. 6 holograms.
+ * complex_dev: NULL, or complex64 (interleaved re, im float32) [nlambda][wy][wx]
+ * receiving V itself including the prefactor K and the output chirp of Eq. 6.
+ * Both 16-byte aligned. */
+SSOCT_API ssoct_status ssoct_reconstruct_volume(ssoct_plan plan, float* vol_dev, void* complex_dev,
+                                                void* stream);
+
+/* Same, from nlambda frames already in device memory: frames_dev uint16
+ * [nlambda][ny][nx], 16-byte aligned, frame t taken at wavelength lambda_m[t].
+ * The ring is not touched. */
+SSOCT_API ssoct_status ssoct_reconstruct_frames(ssoct_plan plan, const uint16_t* frames_dev,
+                                                float* vol_dev, void* complex_dev, void* stream);
+
+/* The three orthogonal cuts of a volume written by a reconstruct call with this
+ * plan (text after Eq. 7; Fig. 5): xy[wy][wx] = P(x, y, z0), xz[nlambda][wx] =
+ * P(x, y0, z), yz[nlambda][wy] = P(x0, y, z), coordinates in window pixels and
+ * depth bins.  Any output pointer may be NULL to skip that cut.  EINVAL if an
+ * index is outside the volume. */
+SSOCT_API ssoct_status ssoct_get_cuts(ssoct_plan plan, const float* vol_dev, int x0, int y0, int z0,
+                                      float* xy_dev, float* xz_dev, float* yz_dev, void* stream);
+
+/* Wait for `stream` and report what the kernels recorded: ETIMEOUT if a kernel
+ * gave up waiting on its work queue (its output is then incomplete), ECUDA on a
+ * CUDA error, else OK.  Clears the recorded error. */
+SSOCT_API ssoct_status ssoct_sync(ssoct_plan plan, void* stream);
+
+/* Stage timing.  enable != 0: every reconstruct call from now on records CUDA
+ * events on its stream around its lateral kernel (Eq. 5 + Eq. 6) and its axial
+ * kernel (Eq. 7 + envelope); accumulated times restart at zero.  enable == 0
+ * stops recording.  Host only until the next reconstruct call. */
+SSOCT_API ssoct_status ssoct_profile(ssoct_plan plan, int enable);
+
+/* Wait for the recorded events and return the summed kernel times (ms) and the
+ * number of reconstruct calls recorded since ssoct_profile(plan, 1).  Any output
+ * pointer may be NULL. */
+SSOCT_API ssoct_status ssoct_profile_read(ssoct_plan plan, double* lateral_ms, double* axial_ms, int* calls);
+
+/* Message for the last non-OK status returned on this plan ("" if none). */
+SSOCT_API const char* ssoct_last_error(ssoct_plan plan);
+
+/* Name of a status code. */
+SSOCT_API const char* ssoct_status_string(ssoct_status s);
+
+/* Release the plan's host memory.  The workspace stays the caller's. */
+SSOCT_API void ssoct_destroy_plan(ssoct_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSOCT_H */

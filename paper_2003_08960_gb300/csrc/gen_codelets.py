@@ -1,0 +1,226 @@
+#!/usr/bin/env python3
+"""Writes fft_codelets.cuh: straight-line in-register DFTs for the CUDA kernels.
+
+Build step of the library (run by the package's build script).  For each size R
+in SIZES and each sign, it emits
+
+    template<> struct Dft<R, SIGN> {
+      template<int ST, int OFF> static __host__ __device__ __forceinline__ void run(float2* x);
+    };
+
+which replaces x[OFF + k*ST], k = 0..R-1, by sum_j x[OFF + j*ST] exp(SIGN 2 pi i j k / R)
+(unnormalised, natural order in and out).  Indices are compile-time constants, so
+a register array passed in stays in registers.
+
+Power-of-two sizes use radix-2 decimation in time with the trivial twiddles
+(1, +-i, (+-1 +- i)/sqrt 2) expanded into additions; sizes 3 and 5 use the
+direct real/imaginary symmetric form; composite sizes with a factor 3 or 5 use
+one mixed-radix (Cooley-Tukey) split.  Twiddle constants are computed here in
+float64 and rounded once to float32.
+"""
+
+import math
+import os
+import sys
+
+SIZES = [2, 3, 4, 5, 6, 8, 10, 12, 16, 20, 24, 25, 32, 40]
+
+
+def f32(v: float) -> str:
+    import struct
+    r = struct.unpack("f", struct.pack("f", v))[0]
+    s = repr(float(r))
+    if "e" not in s and "." not in s:
+        s += ".0"
+    return s + "f"
+
+
+class Gen:
+    def __init__(self):
+        self.lines = []
+        self.n = 0
+
+    def var(self):
+        self.n += 1
+        return f"v{self.n}"
+
+    def emit(self, s):
+        self.lines.append("    " + s)
+
+    # complex helpers producing new SSA names ---------------------------------
+    def add(self, a, b):
+        v = self.var()
+        self.emit(f"const float2 {v} = make_float2({a}.x + {b}.x, {a}.y + {b}.y);")
+        return v
+
+    def sub(self, a, b):
+        v = self.var()
+        self.emit(f"const float2 {v} = make_float2({a}.x - {b}.x, {a}.y - {b}.y);")
+        return v
+
+    def twiddle(self, a, k, n, sign):
+        """a * exp(sign 2 pi i k / n), with the trivial cases expanded."""
+        k %= n
+        if k == 0:
+            return a
+        g = math.gcd(k, n)
+        kk, nn = k // g, n // g
+        v = self.var()
+        s = sign
+        if nn == 2:
+            self.emit(f"const float2 {v} = make_float2(-{a}.x, -{a}.y);")
+        elif nn == 4:
+            # exp(s i pi/2 * kk): kk = 1 -> s i ; kk = 3 -> -s i
+            q = s if kk == 1 else -s
+            if q > 0:
+                self.emit(f"const float2 {v} = make_float2(-{a}.y, {a}.x);")
+            else:
+                self.emit(f"const float2 {v} = make_float2({a}.y, -{a}.x);")
+        elif nn == 8:
+            r = f32(math.sqrt(0.5))
+            c = math.cos(2 * math.pi * kk / 8)
+            sn = s * math.sin(2 * math.pi * kk / 8)
+            cs = "+" if c > 0 else "-"
+            # (a.x + i a.y)(c + i sn) with |c| = |sn| = r
+            if sn > 0:
+                re = f"{cs}{a}.x - {a}.y"
+                im = f"{cs}{a}.y + {a}.x"
+            else:
+                re = f"{cs}{a}.x + {a}.y"
+                im = f"{cs}{a}.y - {a}.x"
+            re = re.lstrip("+")
+            im = im.lstrip("+")
+            self.emit(f"const float2 {v} = make_float2(({re}) * {r}, ({im}) * {r});")
+        else:
+            c = f32(math.cos(2 * math.pi * kk / nn))
+            sn = f32(s * math.sin(2 * math.pi * kk / nn))
+            self.emit(f"const float2 {v} = make_float2(fmaf({a}.x, {c}, -{a}.y * {sn}), "
+                      f"fmaf({a}.x, {sn}, {a}.y * {c}));")
+        return v
+
+    # DFTs ---------------------------------------------------------------------
+    def dft(self, xs, sign):
+        n = len(xs)
+        if n == 1:
+            return list(xs)
+        if n == 2:
+            return [self.add(xs[0], xs[1]), self.sub(xs[0], xs[1])]
+        if n == 3:
+            return self.dft3(xs, sign)
+        if n == 5:
+            return self.dft5(xs, sign)
+        if n % 2 == 0 and (n & (n - 1)) == 0:
+            ev = self.dft(xs[0::2], sign)
+            od = self.dft(xs[1::2], sign)
+            out = [None] * n
+            for k in range(n // 2):
+                t = self.twiddle(od[k], k, n, sign)
+                out[k] = self.add(ev[k], t)
+                out[k + n // 2] = self.sub(ev[k], t)
+            return out
+        # mixed radix: n = p * m with p the smallest prime factor in {2,3,5}
+        for p in (2, 3, 5):
+            if n % p == 0:
+                break
+        else:
+            raise ValueError(n)
+        m = n // p
+        # decimation in time: x[j] with j = p*j2 + j1 ... use x[j1 + p*j2]
+        sub_out = [self.dft(xs[j1::p], sign) for j1 in range(p)]   # each length m, index k2
+        out = [None] * n
+        for k2 in range(m):
+            col = [self.twiddle(sub_out[j1][k2], j1 * k2, n, sign) for j1 in range(p)]
+            res = self.dft(col, sign)                               # length p, index k1
+            for k1 in range(p):
+                out[k2 + m * k1] = res[k1]
+        return out
+
+    def dft3(self, xs, sign):
+        a, b, c = xs
+        s = self.add(b, c)
+        d = self.sub(b, c)
+        y0 = self.add(a, s)
+        # y1 = a - s/2 + sign * i * (sqrt3/2) * (b - c);  y2 = a - s/2 - ...
+        h = self.var()
+        self.emit(f"const float2 {h} = make_float2(fmaf({s}.x, -0.5f, {a}.x), fmaf({s}.y, -0.5f, {a}.y));")
+        r = f32(sign * math.sqrt(3.0) / 2.0)
+        y1 = self.var()
+        y2 = self.var()
+        self.emit(f"const float2 {y1} = make_float2(fmaf(-{d}.y, {r}, {h}.x), fmaf({d}.x, {r}, {h}.y));")
+        self.emit(f"const float2 {y2} = make_float2(fmaf({d}.y, {r}, {h}.x), fmaf(-{d}.x, {r}, {h}.y));")
+        return [y0, y1, y2]
+
+    def dft5(self, xs, sign):
+        x0, x1, x2, x3, x4 = xs
+        s1 = self.add(x1, x4)
+        d1 = self.sub(x1, x4)
+        s2 = self.add(x2, x3)
+        d2 = self.sub(x2, x3)
+        y0 = self.var()
+        self.emit(f"const float2 {y0} = make_float2({x0}.x + {s1}.x + {s2}.x, {x0}.y + {s1}.y + {s2}.y);")
+        c1, c2 = math.cos(2 * math.pi / 5), math.cos(4 * math.pi / 5)
+        n1, n2 = sign * math.sin(2 * math.pi / 5), sign * math.sin(4 * math.pi / 5)
+        # y_k = x0 + s1 cos(2pi k/5) + s2 cos(4pi k/5) + i [d1 sin(2pi k/5) + d2 sin(4pi k/5)] * sign
+        outs = [y0]
+        coef = {1: (c1, c2, n1, n2), 2: (c2, c1, n2, -n1)}
+        tmp = {}
+        for k in (1, 2):
+            ca, cb, sa, sb = coef[k]
+            re = self.var()
+            im = self.var()
+            self.emit(f"const float2 {re} = make_float2(fmaf({s1}.x, {f32(ca)}, fmaf({s2}.x, {f32(cb)}, {x0}.x)), "
+                      f"fmaf({s1}.y, {f32(ca)}, fmaf({s2}.y, {f32(cb)}, {x0}.y)));")
+            self.emit(f"const float2 {im} = make_float2(fmaf({d1}.x, {f32(sa)}, {d2}.x * {f32(sb)}), "
+                      f"fmaf({d1}.y, {f32(sa)}, {d2}.y * {f32(sb)}));")
+            tmp[k] = (re, im)
+        # multiply im-part by i: i*(u) = (-u.y, u.x)
+        for k in (1, 2):
+            re, im = tmp[k]
+            v = self.var()
+            self.emit(f"const float2 {v} = make_float2({re}.x - {im}.y, {re}.y + {im}.x);")
+            tmp[k] = tmp[k] + (v,)
+        for k in (3, 4):
+            re, im = tmp[5 - k][:2]
+            v = self.var()
+            self.emit(f"const float2 {v} = make_float2({re}.x + {im}.y, {re}.y - {im}.x);")
+            tmp[k] = (None, None, v)
+        return [y0, tmp[1][2], tmp[2][2], tmp[3][2], tmp[4][2]]
+
+
+def codelet(n, sign):
+    g = Gen()
+    ins = []
+    for k in range(n):
+        v = f"x{k}"
+        g.emit(f"const float2 {v} = x[OFF + {k} * ST];")
+        ins.append(v)
+    outs = g.dft(ins, sign)
+    for k, v in enumerate(outs):
+        g.emit(f"x[OFF + {k} * ST] = {v};")
+    body = "\n".join(g.lines)
+    return (f"template <> struct Dft<{n}, {sign}> {{\n"
+            f"  template <int ST, int OFF>\n"
+            f"  static __host__ __device__ __forceinline__ void run(float2* x) {{\n{body}\n  }}\n}};\n")
+
+
+def main(out_path):
+    parts = [
+        "// Generated by gen_codelets.py: straight-line in-register DFTs.  Do not edit.\n",
+        "#pragma once\n#include <cuda_runtime.h>\n\nnamespace ssoct {\n",
+        "template <int N, int SIGN> struct Dft;\n",
+        "template <int SIGN> struct Dft<1, SIGN> {\n  template <int ST, int OFF>\n"
+        "  static __host__ __device__ __forceinline__ void run(float2*) {}\n};\n",
+    ]
+    for n in SIZES:
+        for sign in (1, -1):
+            parts.append(codelet(n, sign))
+    parts.append("}  // namespace ssoct\n")
+    text = "\n".join(parts)
+    if os.path.exists(out_path) and open(out_path).read() == text:
+        return
+    with open(out_path, "w") as f:
+        f.write(text)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else os.path.join(os.path.dirname(__file__), "fft_codelets.cuh"))

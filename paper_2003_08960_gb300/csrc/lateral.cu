@@ -1,0 +1,263 @@
+// Lateral stage: chromatic rescale (Eq. 5) + Fresnel transform (Eq. 6) of every
+// frame of a sweep, as one persistent kernel.
+//
+// Work items, taken from a device ticket counter in the order LateralSchedule
+// defines:
+//  * row item (frame f, band of rows): stage the input rows the band needs in
+//    shared memory as float, resample them with the frame's separable linear-
+//    interpolation taps, multiply by the input chirp (centring phase folded in),
+//    run the Nx-point row DFT in registers (N2-point DFT per thread, twiddle,
+//    exchange through shared memory, N1-point DFTs), multiply by the row's y
+//    chirp and store the window columns into an L2-resident scratch slot;
+//  * column item (frame f, band of columns): after every row item of f has
+//    signalled, load the band from the scratch slot, run the Ny-point column DFT
+//    the same way, keep the window rows and write them into the sweep-axis
+//    intermediate [wy][tile][t][32] that the axial kernel streams.
+// The scratch ring holds `slots` frames, so the row-transformed frames never
+// leave L2: only the uint16 input is read from HBM and only the windowed
+// complex hologram is written to it.
+#include <cstdio>
+
+#include "fft_common.cuh"
+
+namespace ssoct {
+namespace {
+
+constexpr unsigned kSpinLimit = 1u << 24;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+// One thread waits until *ctr >= target.  Bounded: on timeout it records
+// kErrTimeout, raises the abort flag and returns false; it also returns false
+// as soon as another CTA raised the abort flag.
+__device__ bool wait_counter(const unsigned* ctr, unsigned target, Counters* c) {
+  if (ld_acquire_gpu(ctr) >= target) return true;
+  const unsigned long long t0 = global_timer_ns();
+  for (unsigned it = 0;; ++it) {
+    if (ld_acquire_gpu(ctr) >= target) return true;
+    if (*(volatile unsigned*)&c->abort) return false;
+    if (it > kSpinLimit || global_timer_ns() - t0 > kWaitNs) {
+      atomicCAS(&c->err, 0u, kErrTimeout);
+      atomicExch(&c->abort, 1u);
+      return false;
+    }
+    __nanosleep(128);
+  }
+}
+
+// Row item: rows [item*RPI, item*RPI + RPI) of frame f.
+template <int NX, int NY>
+__device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item, unsigned char* smem,
+                                         int* s_flag) {
+  constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
+  constexpr int RPI = kThreads / N1;
+  constexpr int LD = N1 + 1;  // padded exchange row: conflict-free transposed reads
+  const int tid = threadIdx.x;
+  const int r = tid / N1;
+  const int j1 = tid % N1;
+  const int row0 = item * RPI;
+  const int y = row0 + r;
+  const Tap* yt = p.ytab + (size_t)f * NY;
+  const int jlo = yt[row0].base;
+  const int jhi = yt[row0 + RPI - 1].base + 1;
+  const int nrows = jhi - jlo + 1;
+  const int fr = (p.ring_start + f) % p.nl;
+  // 1. stage input rows jlo..jhi as float (8 pixels per 16-byte load)
+  float* stage = reinterpret_cast<float*>(smem);
+  {
+    const uint4* s4 = reinterpret_cast<const uint4*>(p.frames + ((size_t)fr * NY + jlo) * NX);
+    float4* d4 = reinterpret_cast<float4*>(stage);
+    const int nvec = nrows * (NX / 8);
+    for (int i = tid; i < nvec; i += kThreads) {
+      const uint4 v = __ldg(s4 + i);
+      d4[2 * i] = make_float4(u16lo_to_f(v.x), u16hi_to_f(v.x), u16lo_to_f(v.y), u16hi_to_f(v.y));
+      d4[2 * i + 1] = make_float4(u16lo_to_f(v.z), u16hi_to_f(v.z), u16lo_to_f(v.w), u16hi_to_f(v.w));
+    }
+  }
+  __syncthreads();
+  // 2. Eq. 5 resample x input chirp, elements n = j1 + N1 * j2 of row y
+  float2 a[N2];
+  {
+    const Tap ty = yt[y];
+    const float* r0 = stage + (ty.base - jlo) * NX;
+    const float* r1 = r0 + NX;
+    const float4* xt = reinterpret_cast<const float4*>(p.xtab + (size_t)f * NX);
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) {
+      const int n = j1 + N1 * j2;
+      const float4 t = __ldg(xt + n);
+      const int bx = __float_as_int(t.x);
+      const float v0 = fmaf(t.y, r0[bx], t.z * r0[bx + 1]);
+      const float v1 = fmaf(t.y, r1[bx], t.z * r1[bx + 1]);
+      const float v = fmaf(ty.w0, v0, ty.w1 * v1);
+      const float2 c = ldg2(p.cx + n);
+      a[j2] = make_float2(v * c.x, v * c.y);
+    }
+  }
+  // 3. row DFT (+ sign of Eq. 6), first factor in registers
+  Dft<N2, 1>::template run<1, 0>(a);
+  {
+    const float2 cyv = ldg2(p.cy + y);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(ldg2(p.twx + k2 * N1 + j1), cyv));
+  }
+  __syncthreads();  // staging rows are dead: the exchange buffer reuses them
+  float2* exr = reinterpret_cast<float2*>(smem) + r * (N2 * LD);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) exr[k2 * LD + j1] = a[k2];
+  __syncwarp();  // a row's N1 threads lie in one warp
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = exr[k2 * LD + jj];
+    Dft<N1, 1>::template run<1, i * N1>(a);
+  });
+  // 4. the scratch slot of frame f must be free (its previous frame's columns done)
+  if (f >= p.sch.slots) {
+    if (tid == 0) *s_flag = wait_counter(p.cols_done + (f - p.sch.slots), (unsigned)p.sch.n_col, p.ctr) ? 0 : 1;
+    __syncthreads();
+    if (*s_flag) return false;
+  }
+  float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const int kw = k2 + N2 * k1 - p.x0;
+      if (kw >= 0 && kw < p.wx) __stcg(dst + kw, a[i * N1 + k1]);
+    }
+  });
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    atomicAdd(p.rows_done + f, 1u);
+  }
+  return true;
+}
+
+// Column item: window columns [item*BC, item*BC + BC) of frame f.
+template <int NY>
+__device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item, unsigned char* smem,
+                                         int* s_flag) {
+  constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
+  constexpr int BC = kThreads / N1;
+  const int tid = threadIdx.x;
+  const int b = tid % BC;
+  const int j1 = tid / BC;
+  if (tid == 0) *s_flag = wait_counter(p.rows_done + f, (unsigned)p.sch.n_row, p.ctr) ? 0 : 1;
+  __syncthreads();
+  if (*s_flag) return false;
+  const int c0 = item * BC;
+  const float2* src = p.scratch + (size_t)(f % p.sch.slots) * NY * p.wxp + c0 + b;
+  float2 a[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) a[j2] = __ldcg(src + (size_t)(j1 + N1 * j2) * p.wxp);
+  Dft<N2, 1>::template run<1, 0>(a);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(p.twy + k2 * N1 + j1));
+  float2* ex = reinterpret_cast<float2*>(smem);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * BC + b] = a[k2];
+  __syncthreads();
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * BC + b];
+    Dft<N1, 1>::template run<1, i * N1>(a);
+  });
+  const int kxw = c0 + b;
+  if (kxw < p.wx) {
+    float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)f * kTile + (kxw % kTile);
+    const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const int k2 = j1 + N1 * i;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int kyw = k2 + N2 * k1 - p.y0;
+        if (kyw >= 0 && kyw < p.wy) dst[(size_t)kyw * row_pitch] = a[i * N1 + k1];
+      }
+    });
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    atomicAdd(p.cols_done + f, 1u);
+  }
+  return true;
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(kThreads, 1) lateral_kernel(const __grid_constant__ LateralParams p) {
+  static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_ticket;
+  __shared__ int s_flag;
+  const long long total = p.sch.total();
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_ticket = (*(volatile unsigned*)&p.ctr->abort) ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
+    }
+    __syncthreads();
+    const long long k = s_ticket;
+    if (k >= total) break;
+    int kind, f, item;
+    p.sch.decode(k, kind, f, item);
+    const bool ok = kind == 0 ? row_item<NX, NY>(p, f, item, smem, &s_flag)
+                              : col_item<NY>(p, f, item, smem, &s_flag);
+    if (!ok) break;
+  }
+}
+
+template <int NX, int NY>
+size_t smem_for(const Plan& p) {
+  constexpr int N1x = Split<NX>::N1, N2x = Split<NX>::N2;
+  constexpr int N1y = Split<NY>::N1;
+  const size_t stage = (size_t)p.stage_rows * NX * sizeof(float);
+  const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
+  const size_t cols = (size_t)NY * (kThreads / N1y) * sizeof(float2);
+  size_t m = stage > rows ? stage : rows;
+  return m > cols ? m : cols;
+}
+
+template <int NX, int NY>
+cudaError_t launch(const Plan& p, const LateralParams& lp, cudaStream_t s) {
+  const size_t smem = smem_for<NX, NY>(p);
+  cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  long long total = lp.sch.total();
+  int grid = p.num_sms > 0 ? p.num_sms : 1;
+  if (grid > total) grid = (int)total;
+  lateral_kernel<NX, NY><<<grid, kThreads, smem, s>>>(lp);
+  return cudaGetLastError();
+}
+
+#define SSOCT_LATERAL_SIZES(X) \
+  X(64, 64) X(128, 128) X(256, 256) X(512, 512) X(1024, 1024) X(128, 64) X(64, 128)
+
+}  // namespace
+
+bool lateral_supported(int nx, int ny) {
+#define X(a, b) if (nx == a && ny == b) return true;
+  SSOCT_LATERAL_SIZES(X)
+#undef X
+  return false;
+}
+
+size_t lateral_smem_bytes(const Plan& p) {
+#define X(a, b) if (p.nx == a && p.ny == b) return smem_for<a, b>(p);
+  SSOCT_LATERAL_SIZES(X)
+#undef X
+  return 0;
+}
+
+cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s) {
+#define X(a, b) if (p.nx == a && p.ny == b) return launch<a, b>(p, lp, s);
+  SSOCT_LATERAL_SIZES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ssoct

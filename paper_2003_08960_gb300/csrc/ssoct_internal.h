@@ -1,0 +1,180 @@
+// Internal types shared by the host plan code and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ssoct.h"
+
+namespace ssoct {
+
+constexpr int kThreads = 512;          // every lateral-stage CTA has 512 threads
+constexpr int kTile = 32;              // pixels per sweep-axis tile (one x-run)
+
+// FFT length N = N1 * N2 as the kernels split it: an N2-point DFT per thread,
+// a twiddle, an exchange through shared memory, N1-point DFTs (0 = not built).
+__host__ __device__ constexpr int split_n1(int n) {
+  return n == 16 ? 4 : n == 32 ? 4 : n == 64 ? 8 : n == 128 ? 8 : n == 256 ? 16
+       : n == 512 ? 16 : n == 1024 ? 32 : 0;
+}
+
+// Separable linear-interpolation tap for one output coordinate of one frame
+// (Eq. 5): the value is w0 * in[base] + w1 * in[base + 1]; base is clamped so
+// both reads are inside the frame, and a weight is 0 where its tap fell outside.
+struct __align__(16) Tap {
+  int base;
+  float w0;
+  float w1;
+  float pad;
+};
+
+// Device work-queue counters of the lateral kernel (zeroed before each launch).
+struct Counters {
+  unsigned ticket;
+  unsigned abort;
+  unsigned err;
+  unsigned pad[29];
+  // followed by rows_done[nlambda], cols_done[nlambda]
+};
+
+constexpr unsigned kErrTimeout = 1u;
+
+// Order in which the lateral kernel takes its items.  Step s holds the row
+// items of frame s (if s < nl) and then the column items of frame s - lag (if
+// s >= lag).  A column item of frame f waits for every row item of f; a row item
+// of frame f (f >= slots) waits for every column item of f - slots, whose L2
+// scratch slot it reuses.  Both wait on items of earlier tickets, and a ticket
+// is only taken by a running CTA, so the queue always drains (requires
+// slots > lag).
+struct LateralSchedule {
+  int nl;
+  int n_row;   // row items per frame
+  int n_col;   // column items per frame
+  int lag;
+  int slots;
+
+  __host__ __device__ long long total() const { return (long long)nl * (n_row + n_col); }
+
+  __host__ __device__ void decode(long long k, int& kind, int& frame, int& item) const {
+    const long long head = (long long)lag * n_row;
+    if (k < head) {
+      kind = 0;
+      frame = (int)(k / n_row);
+      item = (int)(k % n_row);
+      return;
+    }
+    k -= head;
+    const long long per = n_row + n_col;
+    const long long both = (long long)(nl - lag) * per;
+    if (k < both) {
+      const int step = lag + (int)(k / per);
+      const int r = (int)(k % per);
+      if (r < n_row) {
+        kind = 0;
+        frame = step;
+        item = r;
+      } else {
+        kind = 1;
+        frame = step - lag;
+        item = r - n_row;
+      }
+      return;
+    }
+    k -= both;
+    kind = 1;
+    frame = nl - lag + (int)(k / n_col);
+    item = (int)(k % n_col);
+  }
+};
+
+// Everything the lateral kernel (rescale + chirp + row FFT, column FFT) reads.
+struct LateralParams {
+  const uint16_t* frames;  // gate frame t at frames + ((ring_start + t) % nl) * nx * ny
+  int ring_start;
+  int nx, ny, nl;
+  int x0, y0, wx, wy;      // window
+  int wxp;                 // scratch row pitch (complex elements)
+  int ntx;                 // sweep-axis tiles per window row
+  const Tap* xtab;         // [nl][nx]
+  const Tap* ytab;         // [nl][ny]
+  const float2* cx;        // [nx] input chirp incl. centring phase
+  const float2* cy;        // [ny]
+  const float2* twx;       // [N2x][N1x] row-FFT twiddles
+  const float2* twy;       // [N2y][N1y] column-FFT twiddles
+  float2* scratch;         // [slots][ny][wxp]
+  float2* inter;           // [wy][ntx][nl][32]
+  Counters* ctr;
+  unsigned* rows_done;     // [nl]
+  unsigned* cols_done;     // [nl]
+  LateralSchedule sch;
+  int stage_rows;          // input rows staged per row item (max over items)
+};
+
+struct AxialParams {
+  const float2* inter;     // [wy][ntx][nl][32]
+  float* vol;              // [nl][wy][wx]
+  float2* cplx;            // optional [nl][wy][wx]
+  const float2* twl;       // [N2l][N1l], sign -
+  const float2* ox;        // [wx] output chirp (x), incl. centring phase
+  const float2* oy;        // [wy] output chirp (y) times the prefactor K
+  int nl, wx, wy, ntx;
+  float power_scale;       // |K|^2
+  int magnitude;           // 1: write |V| instead of |V|^2
+};
+
+struct CutsParams {
+  const float* vol;
+  float* xy;
+  float* xz;
+  float* yz;
+  int nl, wx, wy, x0, y0, z0;
+};
+
+// Host-side plan.
+struct Plan {
+  int nx, ny, nl;
+  int x0, y0, wx, wy;
+  unsigned flags;
+  double pitch, z, lambda1;
+  std::vector<double> lambdas;
+  double kre, kim;          // prefactor K
+  double alpha;             // d^2 / (lambda_1 z) = |K|
+  // host tables
+  std::vector<Tap> xtab, ytab;
+  std::vector<float2> cx, cy, ox, oy, twx, twy, twl;
+  // geometry of the device work
+  int n1x, n2x, n1y, n2y, n1l, n2l;
+  int rows_per_item, cols_per_item;
+  int wxp, ntx;
+  int stage_rows;
+  LateralSchedule sch;
+  // workspace layout (byte offsets)
+  size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_ox, off_oy, off_twx, off_twy, off_twl;
+  size_t off_ring, off_scratch, off_inter, ws_bytes;
+  char* ws = nullptr;
+  int device = -1;
+  int num_sms = 0;
+  // frame ring state
+  long long pushed = 0;     // frames in the current gate (capped at nl)
+  int ring_head = 0;        // next ring slot to write
+  long long next_seq = -1;
+  std::string last_error;
+  // stage timing (ssoct_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;  // 3 per recorded call: start, after lateral, after axial
+  size_t events_used = 0;
+};
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s);
+cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s);
+cudaError_t launch_cuts(const CutsParams& cp, cudaStream_t s);
+bool lateral_supported(int nx, int ny);
+bool axial_supported(int nl);
+// Dynamic shared memory of the lateral kernel for a plan (bytes).
+size_t lateral_smem_bytes(const Plan& p);
+
+}  // namespace ssoct

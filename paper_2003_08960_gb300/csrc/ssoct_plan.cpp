@@ -1,0 +1,479 @@
+// Host side of libssoct: plan validation, float64 table construction, workspace
+// layout, frame ring, and the C ABI entry points declared in include/ssoct.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ssoct_internal.h"
+
+using namespace ssoct;
+
+struct ssoct_plan_s {
+  Plan p;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+ssoct_status fail(Plan* p, ssoct_status s, const std::string& msg) {
+  if (p) p->last_error = msg;
+  return s;
+}
+
+ssoct_status cuda_fail(Plan* p, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(p, SSOCT_ECUDA, m);
+}
+
+// exp(i pi r) for r given already reduced to a few units; float64 then rounded once.
+float2 cis_pi(double r) {
+  const double a = kPi * r;
+  return make_float2((float)std::cos(a), (float)std::sin(a));
+}
+
+// Eq. 5 along one axis: output pixel i reads the input at u = c + (i - c) s,
+// c = n / 2, by linear interpolation; a tap outside [0, n) reads 0.
+Tap make_tap(int i, int n, double s) {
+  const double c = n / 2.0;
+  const double u = c + (i - c) * s;
+  const double fl = std::floor(u);
+  const double a = u - fl;
+  const long i0 = (long)fl, i1 = i0 + 1;
+  const double w0 = (i0 >= 0 && i0 < n) ? 1.0 - a : 0.0;
+  const double w1 = (i1 >= 0 && i1 < n) ? a : 0.0;
+  long b = i0 < 0 ? 0 : i0;
+  if (b > n - 2) b = n - 2;
+  double wb = 0.0, wb1 = 0.0;
+  if (i0 == b) wb += w0; else if (i0 == b + 1) wb1 += w0;
+  if (i1 == b) wb += w1; else if (i1 == b + 1) wb1 += w1;
+  Tap t;
+  t.base = (int)b;
+  t.w0 = (float)wb;
+  t.w1 = (float)wb1;
+  t.pad = 0.f;
+  return t;
+}
+
+// Input chirp of Eq. 6 times the centring phase along one axis of length n:
+// exp(-i pi [(k - n/2)^2 alpha + k]); alpha = d^2 / (lambda_1 z).  With it the
+// centred sum over (k - n/2)(m - n/2) / n becomes a plain DFT over k m / n.
+std::vector<float2> input_chirp(int n, double alpha) {
+  std::vector<float2> v(n);
+  for (int k = 0; k < n; ++k) {
+    const double d = k - n / 2.0;
+    const double r = std::fmod(d * d * alpha, 2.0) + (double)(k & 1);
+    v[k] = cis_pi(-r);
+  }
+  return v;
+}
+
+// Output chirp of Eq. 6 on the hologram grid x_m = (m - n/2) d', times the
+// remaining centring phase exp(-i pi (m - n/2)):  exp(-i pi [(m - n/2)^2 / (n^2 alpha) + m - n/2]).
+std::vector<float2> output_chirp(int n, double alpha, int m0, int count) {
+  std::vector<float2> v(count);
+  const double inv = 1.0 / ((double)n * (double)n * alpha);
+  for (int i = 0; i < count; ++i) {
+    const int m = m0 + i;
+    const double d = m - n / 2.0;
+    const double r = std::fmod(d * d * inv, 2.0) + std::fmod(d, 2.0);
+    v[i] = cis_pi(-r);
+  }
+  return v;
+}
+
+// tw[k2][j1] = exp(sign 2 pi i j1 k2 / n) for the n = n1 * n2 split.
+std::vector<float2> twiddles(int n, int n1, int n2, int sign) {
+  std::vector<float2> v((size_t)n1 * n2);
+  for (int k2 = 0; k2 < n2; ++k2)
+    for (int j1 = 0; j1 < n1; ++j1) {
+      const long e = ((long)j1 * k2) % n;
+      v[(size_t)k2 * n1 + j1] = cis_pi(sign * 2.0 * (double)e / n);
+    }
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ssoct_status_string(ssoct_status s) {
+  switch (s) {
+    case SSOCT_OK: return "SSOCT_OK";
+    case SSOCT_EINVAL: return "SSOCT_EINVAL";
+    case SSOCT_ENOMEM: return "SSOCT_ENOMEM";
+    case SSOCT_ECUDA: return "SSOCT_ECUDA";
+    case SSOCT_EAGAIN: return "SSOCT_EAGAIN";
+    case SSOCT_ENOTREADY: return "SSOCT_ENOTREADY";
+    case SSOCT_EDROPPED: return "SSOCT_EDROPPED";
+    case SSOCT_ETIMEOUT: return "SSOCT_ETIMEOUT";
+    case SSOCT_EUNSUPPORTED: return "SSOCT_EUNSUPPORTED";
+  }
+  return "SSOCT_?";
+}
+
+ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, double z_m,
+                               const double* lambda_m, const ssoct_window* win, unsigned flags,
+                               ssoct_plan* out) {
+  if (!out) return SSOCT_EINVAL;
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nlambda < 1 || !lambda_m) return SSOCT_EINVAL;
+  if ((nx & 1) || (ny & 1)) return SSOCT_EINVAL;  // the centred grid needs an even size
+  if (!(pitch_m > 0.0) || !std::isfinite(pitch_m) || z_m == 0.0 || !std::isfinite(z_m))
+    return SSOCT_EINVAL;
+  for (int t = 0; t < nlambda; ++t)
+    if (!(lambda_m[t] > 0.0) || !std::isfinite(lambda_m[t])) return SSOCT_EINVAL;
+  if (flags & ~SSOCT_FLAG_MAGNITUDE) return SSOCT_EINVAL;
+  ssoct_window w = win ? *win : ssoct_window{0, 0, nx, ny};
+  if (w.x0 < 0 || w.y0 < 0 || w.wx < 1 || w.wy < 1 || w.x0 + w.wx > nx || w.y0 + w.wy > ny)
+    return SSOCT_EINVAL;
+  if (!lateral_supported(nx, ny) || !axial_supported(nlambda)) return SSOCT_EUNSUPPORTED;
+
+  ssoct_plan h = new (std::nothrow) ssoct_plan_s();
+  if (!h) return SSOCT_ENOMEM;
+  Plan& p = h->p;
+  p.nx = nx; p.ny = ny; p.nl = nlambda;
+  p.x0 = w.x0; p.y0 = w.y0; p.wx = w.wx; p.wy = w.wy;
+  p.flags = flags;
+  p.pitch = pitch_m; p.z = z_m;
+  p.lambdas.assign(lambda_m, lambda_m + nlambda);
+  p.lambda1 = lambda_m[0];
+  p.alpha = pitch_m * pitch_m / (p.lambda1 * z_m);
+  {
+    // K = (i / (lambda_1 z)) exp(-i k_1 z) d^2; k_1 z = 2 pi z / lambda_1 reduced mod 1 turn.
+    const double turns = std::fmod(z_m / p.lambda1, 1.0);
+    const double ph = -2.0 * kPi * turns;
+    const double mag = pitch_m * pitch_m / (p.lambda1 * z_m);
+    // i * exp(i ph) = exp(i (ph + pi/2))
+    p.kre = mag * std::cos(ph + 0.5 * kPi);
+    p.kim = mag * std::sin(ph + 0.5 * kPi);
+  }
+
+  // Eq. 5 taps, per frame and axis (ratio lambda_t / lambda_1).
+  p.xtab.resize((size_t)nlambda * nx);
+  p.ytab.resize((size_t)nlambda * ny);
+  for (int t = 0; t < nlambda; ++t) {
+    const double s = lambda_m[t] / p.lambda1;
+    for (int i = 0; i < nx; ++i) p.xtab[(size_t)t * nx + i] = make_tap(i, nx, s);
+    for (int j = 0; j < ny; ++j) p.ytab[(size_t)t * ny + j] = make_tap(j, ny, s);
+  }
+  // Eq. 6 chirps.  alpha x (k - n/2)^2 is the chirp phase / pi.
+  p.cx = input_chirp(nx, p.alpha);
+  p.cy = input_chirp(ny, p.alpha);
+  p.ox = output_chirp(nx, p.alpha, p.x0, p.wx);
+  {
+    std::vector<float2> oy = output_chirp(ny, p.alpha, p.y0, p.wy);
+    // fold K into the y factor (float64 product, rounded once)
+    const double c = ny / 2.0;
+    const double inv = 1.0 / ((double)ny * (double)ny * p.alpha);
+    for (int i = 0; i < p.wy; ++i) {
+      const int m = p.y0 + i;
+      const double d = m - c;
+      const double r = std::fmod(d * d * inv, 2.0) + std::fmod(d, 2.0);
+      const double cr = std::cos(-kPi * r), ci = std::sin(-kPi * r);
+      oy[i] = make_float2((float)(p.kre * cr - p.kim * ci), (float)(p.kre * ci + p.kim * cr));
+    }
+    p.oy = oy;
+  }
+  p.n1x = split_n1(nx); p.n2x = nx / p.n1x;
+  p.n1y = split_n1(ny); p.n2y = ny / p.n1y;
+  p.n1l = split_n1(nlambda); p.n2l = nlambda / p.n1l;
+  p.twx = twiddles(nx, p.n1x, p.n2x, +1);
+  p.twy = twiddles(ny, p.n1y, p.n2y, +1);
+  p.twl = twiddles(nlambda, p.n1l, p.n2l, -1);
+
+  // Work decomposition of the lateral kernel.
+  p.rows_per_item = kThreads / p.n1x;
+  if (p.rows_per_item > ny) p.rows_per_item = ny;
+  p.cols_per_item = kThreads / p.n1y;
+  p.wxp = (int)align_up((size_t)p.wx, 64);
+  p.ntx = (p.wx + kTile - 1) / kTile;
+  p.sch.nl = nlambda;
+  p.sch.n_row = ny / p.rows_per_item;
+  p.sch.n_col = (p.wx + p.cols_per_item - 1) / p.cols_per_item;
+  p.sch.lag = nlambda >= 2 ? 1 : 0;
+  p.sch.slots = p.sch.lag + 2;
+  // input rows a row item stages: from the first row's base to the last row's base + 1
+  int st = 0;
+  for (int t = 0; t < nlambda; ++t)
+    for (int it = 0; it < p.sch.n_row; ++it) {
+      const Tap& a = p.ytab[(size_t)t * ny + it * p.rows_per_item];
+      const Tap& b = p.ytab[(size_t)t * ny + it * p.rows_per_item + p.rows_per_item - 1];
+      const int rows = b.base + 1 - a.base + 1;
+      if (rows > st) st = rows;
+    }
+  p.stage_rows = st;
+  if (lateral_smem_bytes(p) > 227u * 1024u) {
+    delete h;
+    return SSOCT_EUNSUPPORTED;  // rescale ratio too far from 1 for the staging buffer
+  }
+
+  // Workspace layout.
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
+  p.off_ctr = take(sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)nlambda);
+  p.off_xtab = take(sizeof(Tap) * p.xtab.size());
+  p.off_ytab = take(sizeof(Tap) * p.ytab.size());
+  p.off_cx = take(sizeof(float2) * nx);
+  p.off_cy = take(sizeof(float2) * ny);
+  p.off_ox = take(sizeof(float2) * p.wx);
+  p.off_oy = take(sizeof(float2) * p.wy);
+  p.off_twx = take(sizeof(float2) * p.twx.size());
+  p.off_twy = take(sizeof(float2) * p.twy.size());
+  p.off_twl = take(sizeof(float2) * p.twl.size());
+  p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
+  p.off_scratch = take(sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
+  p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
+  p.ws_bytes = off;
+  *out = h;
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_plan_info(ssoct_plan h, ssoct_plan_info_t* info) {
+  if (!h || !info) return SSOCT_EINVAL;
+  const Plan& p = h->p;
+  info->nx = p.nx; info->ny = p.ny; info->nlambda = p.nl;
+  info->window = ssoct_window{p.x0, p.y0, p.wx, p.wy};
+  info->lambda1_m = p.lambda1;
+  info->dprime_x_m = p.lambda1 * p.z / (p.nx * p.pitch);
+  info->dprime_y_m = p.lambda1 * p.z / (p.ny * p.pitch);
+  const int nmax = p.nx > p.ny ? p.nx : p.ny;
+  info->z_b_m = nmax * p.pitch * p.pitch / p.lambda1;
+  info->aliased_chirp = std::fabs(p.z) < info->z_b_m ? 1 : 0;
+  info->prefactor_re = p.kre;
+  info->prefactor_im = p.kim;
+  info->workspace_bytes = p.ws_bytes;
+  info->ring_slots = p.sch.slots;
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_workspace_size(ssoct_plan h, size_t* bytes) {
+  if (!h || !bytes) return SSOCT_EINVAL;
+  *bytes = h->p.ws_bytes;
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!dev_ptr || ((uintptr_t)dev_ptr % kAlign)) return fail(&p, SSOCT_EINVAL, "workspace NULL or not 256-byte aligned");
+  if (bytes < p.ws_bytes) return fail(&p, SSOCT_ENOMEM, "workspace smaller than ssoct_workspace_size");
+  cudaError_t e = cudaGetDevice(&p.device);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "cudaGetDevice");
+  e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "cudaDeviceGetAttribute");
+  char* ws = (char*)dev_ptr;
+  struct Up { size_t off; const void* src; size_t n; } ups[] = {
+      {p.off_xtab, p.xtab.data(), sizeof(Tap) * p.xtab.size()},
+      {p.off_ytab, p.ytab.data(), sizeof(Tap) * p.ytab.size()},
+      {p.off_cx, p.cx.data(), sizeof(float2) * p.cx.size()},
+      {p.off_cy, p.cy.data(), sizeof(float2) * p.cy.size()},
+      {p.off_ox, p.ox.data(), sizeof(float2) * p.ox.size()},
+      {p.off_oy, p.oy.data(), sizeof(float2) * p.oy.size()},
+      {p.off_twx, p.twx.data(), sizeof(float2) * p.twx.size()},
+      {p.off_twy, p.twy.data(), sizeof(float2) * p.twy.size()},
+      {p.off_twl, p.twl.data(), sizeof(float2) * p.twl.size()},
+  };
+  for (const Up& u : ups) {
+    e = cudaMemcpy(ws + u.off, u.src, u.n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "table upload");
+  }
+  e = cudaMemset(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "counter reset");
+  p.ws = ws;
+  p.pushed = 0;
+  p.ring_head = 0;
+  p.next_seq = -1;
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_push_frames(ssoct_plan h, const uint16_t* frames, int n, int frames_on_device,
+                               int64_t first_seq, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
+  if (!frames || n < 1) return fail(&p, SSOCT_EINVAL, "frames NULL or n < 1");
+  ssoct_status st = SSOCT_OK;
+  if (first_seq >= 0) {
+    if (p.next_seq >= 0 && first_seq != p.next_seq) {
+      // a drop: the current gate can no longer hold consecutive frames
+      p.pushed = 0;
+      p.ring_head = 0;
+      st = SSOCT_EDROPPED;
+    }
+    p.next_seq = first_seq + n;
+  }
+  const size_t fbytes = sizeof(uint16_t) * (size_t)p.nx * p.ny;
+  // only the last nl frames of a long push can survive in the ring
+  int skip = n > p.nl ? n - p.nl : 0;
+  if (skip) {
+    p.ring_head = (p.ring_head + skip) % p.nl;
+    p.pushed += skip;
+  }
+  const cudaMemcpyKind kind = frames_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaStream_t s = (cudaStream_t)stream;
+  int done = skip;
+  while (done < n) {
+    const int run = std::min(n - done, p.nl - p.ring_head);
+    cudaError_t e = cudaMemcpyAsync(p.ws + p.off_ring + fbytes * p.ring_head,
+                                    (const char*)frames + fbytes * done, fbytes * run, kind, s);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "frame copy");
+    done += run;
+    p.ring_head = (p.ring_head + run) % p.nl;
+    p.pushed += run;
+  }
+  if (p.pushed > p.nl) p.pushed = p.nl;
+  if (st != SSOCT_OK) p.last_error = "frame sequence skipped; gate restarted";
+  return st;
+}
+
+static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, float* vol, void* cplx,
+                               cudaStream_t s) {
+  if (!vol || ((uintptr_t)vol % 16) || ((uintptr_t)cplx % 16))
+    return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
+  char* ws = p.ws;
+  LateralParams lp;
+  lp.frames = frames;
+  lp.ring_start = ring_start;
+  lp.nx = p.nx; lp.ny = p.ny; lp.nl = p.nl;
+  lp.x0 = p.x0; lp.y0 = p.y0; lp.wx = p.wx; lp.wy = p.wy;
+  lp.wxp = p.wxp; lp.ntx = p.ntx;
+  lp.xtab = (const Tap*)(ws + p.off_xtab);
+  lp.ytab = (const Tap*)(ws + p.off_ytab);
+  lp.cx = (const float2*)(ws + p.off_cx);
+  lp.cy = (const float2*)(ws + p.off_cy);
+  lp.twx = (const float2*)(ws + p.off_twx);
+  lp.twy = (const float2*)(ws + p.off_twy);
+  lp.scratch = (float2*)(ws + p.off_scratch);
+  lp.inter = (float2*)(ws + p.off_inter);
+  lp.ctr = (Counters*)(ws + p.off_ctr);
+  lp.rows_done = (unsigned*)(ws + p.off_ctr + sizeof(Counters));
+  lp.cols_done = lp.rows_done + p.nl;
+  lp.sch = p.sch;
+  lp.stage_rows = p.stage_rows;
+  cudaError_t e = cudaMemsetAsync(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl, s);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "counter reset");
+  cudaEvent_t* ev = nullptr;
+  if (p.profiling) {
+    if (p.events_used + 3 > p.events.size()) {
+      for (int i = 0; i < 3; ++i) {
+        cudaEvent_t x;
+        e = cudaEventCreate(&x);
+        if (e != cudaSuccess) return cuda_fail(&p, e, "event create");
+        p.events.push_back(x);
+      }
+    }
+    ev = p.events.data() + p.events_used;
+    p.events_used += 3;
+    cudaEventRecord(ev[0], s);
+  }
+  e = launch_lateral(p, lp, s);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "lateral kernel launch");
+  if (ev) cudaEventRecord(ev[1], s);
+  AxialParams ap;
+  ap.inter = lp.inter;
+  ap.vol = vol;
+  ap.cplx = (float2*)cplx;
+  ap.twl = (const float2*)(ws + p.off_twl);
+  ap.ox = (const float2*)(ws + p.off_ox);
+  ap.oy = (const float2*)(ws + p.off_oy);
+  ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
+  ap.power_scale = (float)(p.alpha * p.alpha);
+  ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
+  e = launch_axial(p, ap, s);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "axial kernel launch");
+  if (ev) cudaEventRecord(ev[2], s);
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_reconstruct_volume(ssoct_plan h, float* vol_dev, void* complex_dev, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
+  if (p.pushed < p.nl) return fail(&p, SSOCT_ENOTREADY, "fewer than nlambda frames pushed");
+  // the ring is full: the oldest frame sits at ring_head
+  return run_volume(p, (const uint16_t*)(p.ws + p.off_ring), p.ring_head, vol_dev, complex_dev,
+                    (cudaStream_t)stream);
+}
+
+ssoct_status ssoct_reconstruct_frames(ssoct_plan h, const uint16_t* frames_dev, float* vol_dev,
+                                      void* complex_dev, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
+  if (!frames_dev || ((uintptr_t)frames_dev % 16)) return fail(&p, SSOCT_EINVAL, "frames NULL or not 16-byte aligned");
+  return run_volume(p, frames_dev, 0, vol_dev, complex_dev, (cudaStream_t)stream);
+}
+
+ssoct_status ssoct_get_cuts(ssoct_plan h, const float* vol_dev, int x0, int y0, int z0, float* xy,
+                            float* xz, float* yz, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!vol_dev) return fail(&p, SSOCT_EINVAL, "volume NULL");
+  if (x0 < 0 || x0 >= p.wx || y0 < 0 || y0 >= p.wy || z0 < 0 || z0 >= p.nl)
+    return fail(&p, SSOCT_EINVAL, "cut index outside the volume");
+  if (!xy && !xz && !yz) return SSOCT_OK;
+  CutsParams cp{vol_dev, xy, xz, yz, p.nl, p.wx, p.wy, x0, y0, z0};
+  cudaError_t e = launch_cuts(cp, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "cuts kernel launch");
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_sync(ssoct_plan h, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "stream synchronize");
+  if (!p.ws) return SSOCT_OK;
+  Counters c;
+  e = cudaMemcpy(&c, p.ws + p.off_ctr, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "error word read");
+  if (c.err) {
+    cudaMemset(p.ws + p.off_ctr, 0, sizeof(Counters));
+    return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue");
+  }
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_profile(ssoct_plan h, int enable) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  p.profiling = enable != 0;
+  if (enable) p.events_used = 0;
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_profile_read(ssoct_plan h, double* lateral_ms, double* axial_ms, int* calls) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  double lat = 0.0, ax = 0.0;
+  for (size_t i = 0; i + 2 < p.events_used; i += 3) {
+    float a = 0.f, b = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.events[i + 2]);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "event synchronize");
+    e = cudaEventElapsedTime(&a, p.events[i], p.events[i + 1]);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "event elapsed");
+    e = cudaEventElapsedTime(&b, p.events[i + 1], p.events[i + 2]);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "event elapsed");
+    lat += a;
+    ax += b;
+  }
+  if (lateral_ms) *lateral_ms = lat;
+  if (axial_ms) *axial_ms = ax;
+  if (calls) *calls = (int)(p.events_used / 3);
+  return SSOCT_OK;
+}
+
+const char* ssoct_last_error(ssoct_plan h) { return h ? h->p.last_error.c_str() : ""; }
+
+void ssoct_destroy_plan(ssoct_plan h) {
+  if (!h) return;
+  for (cudaEvent_t e : h->p.events) cudaEventDestroy(e);
+  delete h;
+}
+
+}  // extern "C"

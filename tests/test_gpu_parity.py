@@ -1,0 +1,172 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerance: the FP32 path must match the oracle's complex volume V to a relative
+L2 error <= 1e-5 per volume (also checked on |V|^2 and, separately, on the +1
+order quadrant, where the signal is far below the zero order).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+import pins  # noqa: E402
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ss():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_08960_gb300 import build
+    build.build()
+    import paper_2003_08960_gb300 as ss
+    return ss
+
+
+def _dev(frames):
+    return torch.from_numpy(np.ascontiguousarray(frames).view(np.int16)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _run(ss, w, window=None, method="dense", flags=0):
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, window=window, flags=flags)
+    vol, cplx = plan.reconstruct(_dev(w.frames), complex_out=True)
+    plan.sync()
+    ref = oracle.reconstruct(w.frames, w.pitch, w.z, w.lambdas, window=window, method=method)
+    return plan, vol.cpu().numpy(), cplx.cpu().numpy(), ref
+
+
+def _check(vol, cplx, ref, tol=TOL, quadrant=True):
+    err_v = _rel(cplx.astype(np.complex128), ref)
+    pref = oracle.intensity(ref)
+    err_p = _rel(vol.astype(np.float64), pref)
+    assert err_v <= tol, f"complex volume rel L2 {err_v:.3e}"
+    assert err_p <= 2 * tol, f"|V|^2 rel L2 {err_p:.3e}"
+    if quadrant:
+        nl, wy, wx = ref.shape
+        q = (slice(None), slice(wy // 2 + 2, None), slice(wx // 2 + 2, None))
+        err_q = _rel(cplx[q].astype(np.complex128), ref[q])
+        assert err_q <= 10 * tol, f"+1-order quadrant rel L2 {err_q:.3e}"
+    return err_v
+
+
+def test_tiny_full_window(ss):
+    w = synth.workload("tiny_64x64x32")
+    plan, vol, cplx, ref = _run(ss, w)
+    _check(vol, cplx, ref)
+
+
+def test_tiny_ragged_window(ss):
+    """Off-axis window whose width is not a multiple of the 32-pixel tile."""
+    w = synth.workload("tiny_64x64x32")
+    win = (36, 40, 23, 17)
+    plan, vol, cplx, ref = _run(ss, w, window=win)
+    assert vol.shape == (32, 17, 23)
+    _check(vol, cplx, ref, quadrant=False)
+
+
+@pytest.mark.parametrize("shape", [(128, 64, 16), (64, 128, 64), (128, 128, 128)])
+def test_non_square_and_sizes(ss, shape):
+    nx, ny, nl = shape
+    w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=nx + ny + nl)
+    plan, vol, cplx, ref = _run(ss, w)
+    _check(vol, cplx, ref)
+
+
+def test_point_scatterer_focus_on_gpu(ss):
+    """The closed-form focus position and depth bin, read off the GPU volume."""
+    for case in [(64, 64, 32, 3.3, -5.2, 0.1e-3), (128, 64, 16, -9.6, 7.1, 0.37e-3)]:
+        n, ny, nl, X, Y, d = case
+        frames, lam, sc, dpx, dpy = pins.point_case(n, nl, X, Y, d, ny=ny)
+        plan = ss.Plan(n, ny, nl, pins.PITCH, pins.Z, lam)
+        vol = plan.reconstruct(_dev(frames)).cpu().numpy()
+        mask = np.zeros_like(vol, dtype=bool)
+        mask[:, ny // 2 + 2:, n // 2 + 2:] = True
+        q, y, x = np.unravel_index(np.argmax(np.where(mask, vol, 0)), vol.shape)
+        ex, ey, eq = pins.expected_focus(n, ny, nl, lam, sc, dpx, dpy)
+        assert abs(x - ex) <= 1 and abs(y - ey) <= 1, ((x, y), (ex, ey))
+        dq = abs(q - eq) % nl
+        assert min(dq, nl - dq) <= 1, (q, eq)
+
+
+def test_mid_speckle_512(ss):
+    w = synth.workload("mid_512x512x128")
+    plan, vol, cplx, ref = _run(ss, w, method="fft")
+    _check(vol, cplx, ref)
+
+
+def test_magnitude_flag_and_determinism(ss):
+    w = synth.workload("tiny_64x64x32")
+    p1 = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    p2 = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=ss.SSOCT_FLAG_MAGNITUDE)
+    f = _dev(w.frames)
+    a = p1.reconstruct(f)
+    b = p1.reconstruct(f)
+    m = p2.reconstruct(f)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b), "two runs of the same plan differ"
+    assert torch.allclose(m * m, a, rtol=1e-5, atol=0)
+
+
+def test_ring_path_equals_device_path(ss):
+    w = synth.workload("tiny_64x64x32")
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    ref = plan.reconstruct(_dev(w.frames))
+    with pytest.raises(ss.SsoctError) as e:
+        plan.reconstruct_ring()
+    assert e.value.status == ss.SSOCT_ENOTREADY
+    # push from the host in two pieces, with sequence numbers
+    assert plan.push(w.frames[:10], first_seq=100) == ss.SSOCT_OK
+    assert plan.push(w.frames[10:], first_seq=110) == ss.SSOCT_OK
+    v1 = plan.reconstruct_ring()
+    torch.cuda.synchronize()
+    assert torch.equal(v1, ref)
+    # a wrapped ring: push 5 stray frames then a whole sweep from the device
+    plan.push(_dev(w.frames[:5]), first_seq=142)
+    plan.push(_dev(w.frames), first_seq=147)
+    v2 = plan.reconstruct_ring()
+    torch.cuda.synchronize()
+    assert torch.equal(v2, ref)
+    # a drop restarts the gate
+    assert plan.push(w.frames[:4], first_seq=500) == ss.SSOCT_EDROPPED
+    with pytest.raises(ss.SsoctError):
+        plan.reconstruct_ring()
+
+
+def test_cuts_are_slices(ss):
+    w = synth.workload("tiny_64x64x32")
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, window=(8, 4, 50, 40))
+    vol = plan.reconstruct(_dev(w.frames))
+    xy, xz, yz = plan.cuts(vol, 17, 33, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(xy, vol[5]) and torch.equal(xz, vol[:, 33, :]) and torch.equal(yz, vol[:, :, 17])
+    with pytest.raises(ss.SsoctError):
+        plan.cuts(vol, 50, 0, 0)
+
+
+def test_profile_records_both_kernels(ss):
+    w = synth.workload("tiny_64x64x32")
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    assert ss.ssoct_profile(plan.handle, True) == 0
+    f = _dev(w.frames)
+    for _ in range(3):
+        plan.reconstruct(f)
+    st, lat, ax, calls = ss.ssoct_profile_read(plan.handle)
+    assert st == 0 and calls == 3 and lat > 0 and ax > 0
+
+
+@pytest.mark.slow
+def test_paper_size_1024x1024x256(ss):
+    """Full-size volume in the bench's launch configuration, whole-volume parity."""
+    w = synth.workload("paper_1024x1024x256")
+    plan, vol, cplx, ref = _run(ss, w, method="fft")
+    err = _check(vol, cplx, ref)
+    print(f"1024x1024x256 complex rel L2 = {err:.3e}")
