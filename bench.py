@@ -166,7 +166,11 @@ def run_ssoct(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = synth.workload(WORKLOAD, seed=3 + rank)
+    if args.size:
+        nx, ny, nl = (int(v) for v in args.size.split("x"))
+        w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=3 + rank)
+    else:
+        w = synth.workload(WORKLOAD, seed=3 + rank)
     plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
     h = plan.handle
     stream = torch.cuda.Stream()
@@ -225,6 +229,56 @@ def run_ssoct(args):
     value = world * voxels / (ms * 1e-3) / 1e9
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
+    e2e = _e2e(args, ss, torch, dist, w, h, stream, sp, vol, nl, voxels, world) if not args.no_e2e else None
+    peak, peak_kind = _peaks()
+    lat_bytes = w.nx * w.ny * nl * 2 + voxels * 8
+    ax_bytes = voxels * (8 + 4)
+    kernels = {
+        "lateral": {"ms": lat_ms, "bytes": lat_bytes, "GBps": lat_bytes / (lat_ms * 1e-3) / 1e9},
+        "axial": {"ms": ax_ms, "bytes": ax_bytes, "GBps": ax_bytes / (ax_ms * 1e-3) / 1e9},
+    }
+    for k in kernels.values():
+        k["frac"] = k["GBps"] / peak
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    traffic = _traffic(dom)
+    whole_bytes = lat_bytes + ax_bytes
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_GVOXEL_PER_S, "dtype": "f32",
+        "data": "synthetic (seeded point scatterers, 12-bit, Gaussian read noise)",
+        "config": {"workload": f"{w.nx}x{w.ny}x{nl} sweep, uint16 frames resident in HBM, full window, "
+                               "|V|^2 volume + 3 cuts per step",
+                   "window": [0, 0, wx, wy], "form": "fp32 (paper order)",
+                   "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["GBps"], "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
+                     "traffic": traffic},
+        "whole_step_hbm": {"bytes_per_voxel": whole_bytes / voxels,
+                           "GBps": whole_bytes / (ms * 1e-3) / 1e9,
+                           "frac": whole_bytes / (ms * 1e-3) / 1e9 / peak},
+        "kernels": kernels,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = _sample_frames(w, 15.0)
+        rate, dt, cores = oracle_rate(w, n)
+        out["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"FP64 oracle on the first {n} frames ({w.nx}x{w.ny}x{n} gate), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _e2e(args, ss, torch, dist, w, h, stream, sp, vol, nl, voxels, world):
+    """Same metric through the C ABI with host buffers: pinned host frames are
+    pushed into the plan's ring (H2D), the volume is reconstructed and read back
+    to pinned host memory (D2H), all inside the timed region."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     host_frames = torch.from_numpy(w.frames.view(np.int16)).pin_memory()
     host_vol = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
     e2e_steps = max(3, min(args.steps, 20))
@@ -254,48 +308,8 @@ def run_ssoct(args):
         e2e_ms = float(t.item())
     e2e_value = world * voxels / (e2e_ms * 1e-3) / 1e9
 
-    peak, peak_kind = _peaks()
-    lat_bytes = w.nx * w.ny * nl * 2 + voxels * 8
-    ax_bytes = voxels * (8 + 4)
-    kernels = {
-        "lateral": {"ms": lat_ms, "bytes": lat_bytes, "GBps": lat_bytes / (lat_ms * 1e-3) / 1e9},
-        "axial": {"ms": ax_ms, "bytes": ax_bytes, "GBps": ax_bytes / (ax_ms * 1e-3) / 1e9},
-    }
-    for k in kernels.values():
-        k["frac"] = k["GBps"] / peak
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    traffic = _traffic(dom)
-    whole_bytes = lat_bytes + ax_bytes
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": value / PAPER_GVOXEL_PER_S, "dtype": "f32",
-        "data": "synthetic (seeded point scatterers, 12-bit, Gaussian read noise)",
-        "config": {"workload": f"{w.nx}x{w.ny}x{nl} sweep, uint16 frames resident in HBM, full window, "
-                               "|V|^2 volume + 3 cuts per step",
-                   "window": [0, 0, wx, wy], "form": "fp32 (paper order)",
-                   "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["GBps"], "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
-                     "traffic": traffic},
-        "whole_step_hbm": {"bytes_per_voxel": whole_bytes / voxels,
-                           "GBps": whole_bytes / (ms * 1e-3) / 1e9,
-                           "frac": whole_bytes / (ms * 1e-3) / 1e9 / peak},
-        "kernels": kernels,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_frames.numel() * 2),
-                "d2h_bytes_per_step": int(host_vol.numel() * 4), "ms_per_step": e2e_ms},
-        "gpu_launches": 3 * args.steps,
-        "clocks": clk,
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n = _sample_frames(w, 15.0)
-        rate, dt, cores = oracle_rate(w, n)
-        out["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"FP64 oracle on the first {n} frames ({w.nx}x{w.ny}x{n} gate), {dt:.1f} s"}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_frames.numel() * 2),
+            "d2h_bytes_per_step": int(host_vol.numel() * 4), "ms_per_step": e2e_ms}
 
 
 def _traffic(kernel: str):
@@ -320,6 +334,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ssoct", choices=["ssoct", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", default=None, help="NXxNYxNLAMBDA instead of the 1024x1024x256 workload "
+                                                 "(profiling captures; not a bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -61,16 +61,22 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
   const int jhi = yt[row0 + RPI - 1].base + 1;
   const int nrows = jhi - jlo + 1;
   const int fr = (p.ring_start + f) % p.nl;
-  // 1. stage input rows jlo..jhi as float (8 pixels per 16-byte load)
+  // 1. stage input rows jlo..jhi as float, each row padded with zeros on both
+  //    sides so that taps outside the frame read 0 (8 pixels per 16-byte load)
+  constexpr int SP = NX + 2 * kStagePad;
   float* stage = reinterpret_cast<float*>(smem);
   {
     const uint4* s4 = reinterpret_cast<const uint4*>(p.frames + ((size_t)fr * NY + jlo) * NX);
-    float4* d4 = reinterpret_cast<float4*>(stage);
     const int nvec = nrows * (NX / 8);
     for (int i = tid; i < nvec; i += kThreads) {
       const uint4 v = __ldg(s4 + i);
-      d4[2 * i] = make_float4(u16lo_to_f(v.x), u16hi_to_f(v.x), u16lo_to_f(v.y), u16hi_to_f(v.y));
-      d4[2 * i + 1] = make_float4(u16lo_to_f(v.z), u16hi_to_f(v.z), u16lo_to_f(v.w), u16hi_to_f(v.w));
+      float4* d4 = reinterpret_cast<float4*>(stage + (i / (NX / 8)) * SP + kStagePad + (i % (NX / 8)) * 8);
+      d4[0] = make_float4(u16lo_to_f(v.x), u16hi_to_f(v.x), u16lo_to_f(v.y), u16hi_to_f(v.y));
+      d4[1] = make_float4(u16lo_to_f(v.z), u16hi_to_f(v.z), u16lo_to_f(v.w), u16hi_to_f(v.w));
+    }
+    for (int i = tid; i < nrows; i += kThreads) {
+      stage[i * SP + kStagePad - 1] = 0.f;
+      stage[i * SP + kStagePad + NX] = 0.f;
     }
   }
   __syncthreads();
@@ -78,16 +84,17 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
   float2 a[N2];
   {
     const Tap ty = yt[y];
-    const float* r0 = stage + (ty.base - jlo) * NX;
-    const float* r1 = r0 + NX;
-    const float4* xt = reinterpret_cast<const float4*>(p.xtab + (size_t)f * NX);
+    const float* r0 = stage + (ty.base - jlo) * SP + kStagePad;
+    const float* r1 = r0 + SP;
+    const float2* xt = reinterpret_cast<const float2*>(p.xtab + (size_t)f * NX);
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) {
       const int n = j1 + N1 * j2;
-      const float4 t = __ldg(xt + n);
+      const float2 t = __ldg(xt + n);
       const int bx = __float_as_int(t.x);
-      const float v0 = fmaf(t.y, r0[bx], t.z * r0[bx + 1]);
-      const float v1 = fmaf(t.y, r1[bx], t.z * r1[bx + 1]);
+      const float a0 = r0[bx], a1 = r0[bx + 1], b0 = r1[bx], b1 = r1[bx + 1];
+      const float v0 = fmaf(t.y, a1 - a0, a0);
+      const float v1 = fmaf(t.y, b1 - b0, b0);
       const float v = fmaf(ty.w0, v0, ty.w1 * v1);
       const float2 c = ldg2(p.cx + n);
       a[j2] = make_float2(v * c.x, v * c.y);
@@ -142,6 +149,7 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
                                          int* s_flag) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
+  constexpr int KP = N1 * BC + 8;  // padded k2 block: conflict-free when BC = 8
   const int tid = threadIdx.x;
   const int b = tid % BC;
   const int j1 = tid / BC;
@@ -158,13 +166,13 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(p.twy + k2 * N1 + j1));
   float2* ex = reinterpret_cast<float2*>(smem);
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * BC + b] = a[k2];
+  for (int k2 = 0; k2 < N2; ++k2) ex[k2 * KP + j1 * BC + b] = a[k2];
   __syncthreads();
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
 #pragma unroll
-    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * BC + b];
+    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[k2 * KP + jj * BC + b];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
   const int kxw = c0 + b;
@@ -190,7 +198,7 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kThreads, 1) lateral_kernel(const __grid_constant__ LateralParams p) {
+__global__ void __launch_bounds__(kThreads, 2) lateral_kernel(const __grid_constant__ LateralParams p) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_ticket;
@@ -215,9 +223,10 @@ template <int NX, int NY>
 size_t smem_for(const Plan& p) {
   constexpr int N1x = Split<NX>::N1, N2x = Split<NX>::N2;
   constexpr int N1y = Split<NY>::N1;
-  const size_t stage = (size_t)p.stage_rows * NX * sizeof(float);
+  constexpr int N2y = Split<NY>::N2;
+  const size_t stage = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
   const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
-  const size_t cols = (size_t)NY * (kThreads / N1y) * sizeof(float2);
+  const size_t cols = (size_t)N2y * (N1y * (kThreads / N1y) + 8) * sizeof(float2);
   size_t m = stage > rows ? stage : rows;
   return m > cols ? m : cols;
 }
@@ -228,7 +237,11 @@ cudaError_t launch(const Plan& p, const LateralParams& lp, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   long long total = lp.sch.total();
-  int grid = p.num_sms > 0 ? p.num_sms : 1;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = (p.num_sms > 0 ? p.num_sms : 1) * per_sm;
   if (grid > total) grid = (int)total;
   lateral_kernel<NX, NY><<<grid, kThreads, smem, s>>>(lp);
   return cudaGetLastError();
