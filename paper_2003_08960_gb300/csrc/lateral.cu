@@ -107,7 +107,15 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(ldg2(p.twx + k2 * N1 + j1), cyv));
   }
+  // the scratch slot of frame f must be free (the columns of frame f - slots
+  // done); thread 0 checks before the barrier that retires the staging rows
+  if (tid == 0) {
+    *s_flag = 0;
+    if (f >= p.sch.slots)
+      *s_flag = wait_counter(p.cols_done + (f - p.sch.slots), (unsigned)p.sch.n_col, p.ctr) ? 0 : 1;
+  }
   __syncthreads();  // staging rows are dead: the exchange buffer reuses them
+  if (*s_flag) return false;
   float2* exr = reinterpret_cast<float2*>(smem) + r * (N2 * LD);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) exr[k2 * LD + j1] = a[k2];
@@ -119,12 +127,6 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = exr[k2 * LD + jj];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  // 4. the scratch slot of frame f must be free (its previous frame's columns done)
-  if (f >= p.sch.slots) {
-    if (tid == 0) *s_flag = wait_counter(p.cols_done + (f - p.sch.slots), (unsigned)p.sch.n_col, p.ctr) ? 0 : 1;
-    __syncthreads();
-    if (*s_flag) return false;
-  }
   float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -149,7 +151,9 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
                                          int* s_flag) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
-  constexpr int KP = N1 * BC + 8;  // padded k2 block: conflict-free when BC = 8
+  // padded k2 block: the 16 lanes of a half-warp read 16/BC k2 blocks at once,
+  // shifted by 2*BC banks each, so they never share a bank
+  constexpr int KP = N1 * BC + (BC < 16 ? BC : 0);
   const int tid = threadIdx.x;
   const int b = tid % BC;
   const int j1 = tid / BC;
@@ -198,24 +202,29 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kThreads, 2) lateral_kernel(const __grid_constant__ LateralParams p) {
+__global__ void __launch_bounds__(kThreads, 4) lateral_kernel(const __grid_constant__ LateralParams p) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_ticket;
   __shared__ int s_flag;
   const long long total = p.sch.total();
+  // The next ticket is taken while the current item runs (its atomic round trip
+  // then hides behind the item).  A CTA holds at most one unstarted ticket, and
+  // the lowest unfinished ticket is always the one its CTA is working on, so the
+  // queue still drains.
+  unsigned next = 0;
+  if (threadIdx.x == 0) s_ticket = atomicAdd(&p.ctr->ticket, 1u);
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_ticket = (*(volatile unsigned*)&p.ctr->abort) ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-    }
     __syncthreads();
     const long long k = s_ticket;
     if (k >= total) break;
+    if (threadIdx.x == 0) next = (*(volatile unsigned*)&p.ctr->abort) ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
     int kind, f, item;
     p.sch.decode(k, kind, f, item);
     const bool ok = kind == 0 ? row_item<NX, NY>(p, f, item, smem, &s_flag)
                               : col_item<NY>(p, f, item, smem, &s_flag);
     if (!ok) break;
+    if (threadIdx.x == 0) s_ticket = next;  // every thread read s_ticket before the item's barriers
   }
 }
 
@@ -226,7 +235,8 @@ size_t smem_for(const Plan& p) {
   constexpr int N2y = Split<NY>::N2;
   const size_t stage = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
   const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
-  const size_t cols = (size_t)N2y * (N1y * (kThreads / N1y) + 8) * sizeof(float2);
+  constexpr int BCy = kThreads / N1y;
+  const size_t cols = (size_t)N2y * (N1y * BCy + (BCy < 16 ? BCy : 0)) * sizeof(float2);
   size_t m = stage > rows ? stage : rows;
   return m > cols ? m : cols;
 }

@@ -11,7 +11,7 @@
 
 namespace ssoct {
 
-constexpr int kThreads = 256;          // threads of a lateral-stage CTA (two CTAs per SM)
+constexpr int kThreads = 128;          // threads of a lateral-stage CTA (four CTAs per SM)
 constexpr int kStagePad = 4;           // floats of zero padding on each side of a staged input row
 constexpr int kTile = 32;              // pixels per sweep-axis tile (one x-run)
 
