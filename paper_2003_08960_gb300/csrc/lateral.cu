@@ -45,7 +45,7 @@ __device__ bool wait_counter(const unsigned* ctr, unsigned target, Counters* c) 
 }
 
 // Row item: rows [item*RPI, item*RPI + RPI) of frame f.
-template <int NX, int NY>
+template <int NX, int NY, bool FW>
 __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item, unsigned char* smem,
                                          int* s_flag) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
@@ -86,18 +86,17 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
     const Tap ty = yt[y];
     const float* r0 = stage + (ty.base - jlo) * SP + kStagePad;
     const float* r1 = r0 + SP;
-    const float2* xt = reinterpret_cast<const float2*>(p.xtab + (size_t)f * NX);
+    const float4* xt = reinterpret_cast<const float4*>(p.xtab + (size_t)f * NX);
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) {
       const int n = j1 + N1 * j2;
-      const float2 t = __ldg(xt + n);
+      const float4 t = __ldg(xt + n);
       const int bx = __float_as_int(t.x);
       const float a0 = r0[bx], a1 = r0[bx + 1], b0 = r1[bx], b1 = r1[bx + 1];
       const float v0 = fmaf(t.y, a1 - a0, a0);
       const float v1 = fmaf(t.y, b1 - b0, b0);
       const float v = fmaf(ty.w0, v0, ty.w1 * v1);
-      const float2 c = ldg2(p.cx + n);
-      a[j2] = make_float2(v * c.x, v * c.y);
+      a[j2] = make_float2(v * t.z, v * t.w);
     }
   }
   // 3. row DFT (+ sign of Eq. 6), first factor in registers
@@ -133,20 +132,21 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
     const int k2 = j1 + N1 * i;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
-      const int kw = k2 + N2 * k1 - p.x0;
-      if (kw >= 0 && kw < p.wx) __stcg(dst + kw, a[i * N1 + k1]);
+      if constexpr (FW) {
+        __stcg(dst + k2 + N2 * k1, a[i * N1 + k1]);
+      } else {
+        const int kw = k2 + N2 * k1 - p.x0;
+        if (kw >= 0 && kw < p.wx) __stcg(dst + kw, a[i * N1 + k1]);
+      }
     }
   });
   __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    atomicAdd(p.rows_done + f, 1u);
-  }
+  if (tid == 0) red_release_gpu(p.rows_done + f, 1u);
   return true;
 }
 
 // Column item: window columns [item*BC, item*BC + BC) of frame f.
-template <int NY>
+template <int NY, bool FW>
 __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item, unsigned char* smem,
                                          int* s_flag) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
@@ -188,21 +188,22 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
       const int k2 = j1 + N1 * i;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
-        const int kyw = k2 + N2 * k1 - p.y0;
-        if (kyw >= 0 && kyw < p.wy) dst[(size_t)kyw * row_pitch] = a[i * N1 + k1];
+        if constexpr (FW) {
+          dst[(size_t)(k2 + N2 * k1) * row_pitch] = a[i * N1 + k1];
+        } else {
+          const int kyw = k2 + N2 * k1 - p.y0;
+          if (kyw >= 0 && kyw < p.wy) dst[(size_t)kyw * row_pitch] = a[i * N1 + k1];
+        }
       }
     });
   }
   __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    atomicAdd(p.cols_done + f, 1u);
-  }
+  if (tid == 0) red_release_gpu(p.cols_done + f, 1u);
   return true;
 }
 
-template <int NX, int NY>
-__global__ void __launch_bounds__(kThreads, 4) lateral_kernel(const __grid_constant__ LateralParams p) {
+template <int NX, int NY, bool FW>
+__global__ void __launch_bounds__(kThreads, 2) lateral_kernel(const __grid_constant__ LateralParams p) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_ticket;
@@ -221,8 +222,8 @@ __global__ void __launch_bounds__(kThreads, 4) lateral_kernel(const __grid_const
     if (threadIdx.x == 0) next = (*(volatile unsigned*)&p.ctr->abort) ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
     int kind, f, item;
     p.sch.decode(k, kind, f, item);
-    const bool ok = kind == 0 ? row_item<NX, NY>(p, f, item, smem, &s_flag)
-                              : col_item<NY>(p, f, item, smem, &s_flag);
+    const bool ok = kind == 0 ? row_item<NX, NY, FW>(p, f, item, smem, &s_flag)
+                              : col_item<NY, FW>(p, f, item, smem, &s_flag);
     if (!ok) break;
     if (threadIdx.x == 0) s_ticket = next;  // every thread read s_ticket before the item's barriers
   }
@@ -241,20 +242,27 @@ size_t smem_for(const Plan& p) {
   return m > cols ? m : cols;
 }
 
-template <int NX, int NY>
-cudaError_t launch(const Plan& p, const LateralParams& lp, cudaStream_t s) {
+template <int NX, int NY, bool FW>
+cudaError_t launch_fw(const Plan& p, const LateralParams& lp, cudaStream_t s) {
   const size_t smem = smem_for<NX, NY>(p);
-  cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   long long total = lp.sch.total();
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY, FW>, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = (p.num_sms > 0 ? p.num_sms : 1) * per_sm;
   if (grid > total) grid = (int)total;
-  lateral_kernel<NX, NY><<<grid, kThreads, smem, s>>>(lp);
+  lateral_kernel<NX, NY, FW><<<grid, kThreads, smem, s>>>(lp);
   return cudaGetLastError();
+}
+
+template <int NX, int NY>
+cudaError_t launch(const Plan& p, const LateralParams& lp, cudaStream_t s) {
+  const bool full = p.x0 == 0 && p.y0 == 0 && p.wx == NX && p.wy == NY;
+  return full ? launch_fw<NX, NY, true>(p, lp, s) : launch_fw<NX, NY, false>(p, lp, s);
 }
 
 #define SSOCT_LATERAL_SIZES(X) \

@@ -11,7 +11,7 @@
 
 namespace ssoct {
 
-constexpr int kThreads = 128;          // threads of a lateral-stage CTA (four CTAs per SM)
+constexpr int kThreads = 256;          // threads of a lateral-stage CTA (two CTAs per SM)
 constexpr int kStagePad = 4;           // floats of zero padding on each side of a staged input row
 constexpr int kTile = 32;              // pixels per sweep-axis tile (one x-run)
 
@@ -34,10 +34,13 @@ struct __align__(16) Tap {
 
 // x tap of Eq. 5 against a staged input row padded with zeros on both sides:
 // value = row[base] + w1 * (row[base + 1] - row[base]), base in [-1, n-1]; a tap
-// outside the frame lands on a zero pad (base = -1, w1 = 0 when both do).
-struct __align__(8) TapX {
+// outside the frame lands on a zero pad (base = -1, w1 = 0 when both do).  The
+// column's input chirp of Eq. 6 (centring phase included) rides along, so one
+// 16-byte load serves the pixel.
+struct __align__(16) TapX {
   int base;
   float w1;
+  float cre, cim;
 };
 
 // Device work-queue counters of the lateral kernel (zeroed before each launch).

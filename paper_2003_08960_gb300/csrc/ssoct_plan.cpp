@@ -73,6 +73,7 @@ TapX make_tap_x(int i, int n, double s) {
     t.base = -1;
     t.w1 = 0.f;
   }
+  t.cre = t.cim = 0.f;  // filled with the input chirp by the plan
   return t;
 }
 
@@ -180,6 +181,11 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   }
   // Eq. 6 chirps.  alpha x (k - n/2)^2 is the chirp phase / pi.
   p.cx = input_chirp(nx, p.alpha);
+  for (int t = 0; t < nlambda; ++t)
+    for (int i = 0; i < nx; ++i) {
+      p.xtab[(size_t)t * nx + i].cre = p.cx[i].x;
+      p.xtab[(size_t)t * nx + i].cim = p.cx[i].y;
+    }
   p.cy = input_chirp(ny, p.alpha);
   p.ox = output_chirp(nx, p.alpha, p.x0, p.wx);
   {
@@ -212,7 +218,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.sch.nl = nlambda;
   p.sch.n_row = ny / p.rows_per_item;
   p.sch.n_col = (p.wx + p.cols_per_item - 1) / p.cols_per_item;
-  p.sch.lag = nlambda >= 2 ? 1 : 0;
+  p.sch.lag = nlambda >= 3 ? 2 : nlambda - 1;
   p.sch.slots = p.sch.lag + 2;
   // input rows a row item stages: from the first row's base to the last row's base + 1
   int st = 0;
