@@ -61,6 +61,8 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
   const int jhi = yt[row0 + RPI - 1].base + 1;
   const int nrows = jhi - jlo + 1;
   const int fr = (p.ring_start + f) % p.nl;
+  const unsigned long long pol_first = policy_evict_first();
+  const unsigned long long pol_last = policy_evict_last();
   // 1. stage input rows jlo..jhi as float, each row padded with zeros on both
   //    sides so that taps outside the frame read 0 (8 pixels per 16-byte load)
   constexpr int SP = NX + 2 * kStagePad;
@@ -69,7 +71,7 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
     const uint4* s4 = reinterpret_cast<const uint4*>(p.frames + ((size_t)fr * NY + jlo) * NX);
     const int nvec = nrows * (NX / 8);
     for (int i = tid; i < nvec; i += kThreads) {
-      const uint4 v = __ldg(s4 + i);
+      const uint4 v = ld_nc_hint(s4 + i, pol_first);
       float4* d4 = reinterpret_cast<float4*>(stage + (i / (NX / 8)) * SP + kStagePad + (i % (NX / 8)) * 8);
       d4[0] = make_float4(u16lo_to_f(v.x), u16hi_to_f(v.x), u16lo_to_f(v.y), u16hi_to_f(v.y));
       d4[1] = make_float4(u16lo_to_f(v.z), u16hi_to_f(v.z), u16lo_to_f(v.w), u16hi_to_f(v.w));
@@ -133,10 +135,10 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       if constexpr (FW) {
-        __stcg(dst + k2 + N2 * k1, a[i * N1 + k1]);
+        st_cg_hint(dst + k2 + N2 * k1, a[i * N1 + k1], pol_last);
       } else {
         const int kw = k2 + N2 * k1 - p.x0;
-        if (kw >= 0 && kw < p.wx) __stcg(dst + kw, a[i * N1 + k1]);
+        if (kw >= 0 && kw < p.wx) st_cg_hint(dst + kw, a[i * N1 + k1], pol_last);
       }
     }
   });
@@ -160,11 +162,13 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
   if (tid == 0) *s_flag = wait_counter(p.rows_done + f, (unsigned)p.sch.n_row, p.ctr) ? 0 : 1;
   __syncthreads();
   if (*s_flag) return false;
+  const unsigned long long pol_first = policy_evict_first();
+  const unsigned long long pol_last = policy_evict_last();
   const int c0 = item * BC;
   const float2* src = p.scratch + (size_t)(f % p.sch.slots) * NY * p.wxp + c0 + b;
   float2 a[N2];
 #pragma unroll
-  for (int j2 = 0; j2 < N2; ++j2) a[j2] = __ldcg(src + (size_t)(j1 + N1 * j2) * p.wxp);
+  for (int j2 = 0; j2 < N2; ++j2) a[j2] = ld_cg_hint(src + (size_t)(j1 + N1 * j2) * p.wxp, pol_last);
   Dft<N2, 1>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(p.twy + k2 * N1 + j1));
@@ -189,10 +193,10 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
         if constexpr (FW) {
-          dst[(size_t)(k2 + N2 * k1) * row_pitch] = a[i * N1 + k1];
+          st_cg_hint(dst + (size_t)(k2 + N2 * k1) * row_pitch, a[i * N1 + k1], pol_first);
         } else {
           const int kyw = k2 + N2 * k1 - p.y0;
-          if (kyw >= 0 && kyw < p.wy) dst[(size_t)kyw * row_pitch] = a[i * N1 + k1];
+          if (kyw >= 0 && kyw < p.wy) st_cg_hint(dst + (size_t)kyw * row_pitch, a[i * N1 + k1], pol_first);
         }
       }
     });
@@ -202,6 +206,20 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
   return true;
 }
 
+// L2 prefetch of the input rows a row item will stage (nothing for a column item).
+template <int NX, int NY>
+__device__ __forceinline__ void prefetch_row_input(const LateralParams& p, unsigned t) {
+  int kind, f, item;
+  p.sch.decode(t, kind, f, item);
+  if (kind != 0) return;
+  constexpr int RPI = kThreads / Split<NX>::N1;
+  const Tap* yt = p.ytab + (size_t)f * NY;
+  const int jlo = yt[item * RPI].base;
+  const int jhi = yt[item * RPI + RPI - 1].base + 1;
+  const int fr = (p.ring_start + f) % p.nl;
+  prefetch_l2_bulk(p.frames + ((size_t)fr * NY + jlo) * NX, (unsigned)((jhi - jlo + 1) * NX * sizeof(uint16_t)));
+}
+
 template <int NX, int NY, bool FW>
 __global__ void __launch_bounds__(kThreads, 2) lateral_kernel(const __grid_constant__ LateralParams p) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
@@ -209,23 +227,34 @@ __global__ void __launch_bounds__(kThreads, 2) lateral_kernel(const __grid_const
   __shared__ unsigned s_ticket;
   __shared__ int s_flag;
   const long long total = p.sch.total();
-  // The next ticket is taken while the current item runs (its atomic round trip
-  // then hides behind the item).  A CTA holds at most one unstarted ticket, and
-  // the lowest unfinished ticket is always the one its CTA is working on, so the
-  // queue still drains.
-  unsigned next = 0;
-  if (threadIdx.x == 0) s_ticket = atomicAdd(&p.ctr->ticket, 1u);
+  // Thread 0 keeps the ticket after the current one (t1) in hand and takes the
+  // one after that while the current item runs, so the atomic round trip hides
+  // behind the item; t1's input rows are prefetched into L2 meanwhile.  A CTA
+  // holds at most two unstarted tickets, and the lowest unfinished ticket is
+  // always the one its CTA is working on, so the queue still drains.
+  unsigned t1 = 0xffffffffu;
+  if (threadIdx.x == 0) {
+    s_ticket = atomicAdd(&p.ctr->ticket, 1u);
+    t1 = atomicAdd(&p.ctr->ticket, 1u);
+  }
   for (;;) {
     __syncthreads();
     const long long k = s_ticket;
     if (k >= total) break;
-    if (threadIdx.x == 0) next = (*(volatile unsigned*)&p.ctr->abort) ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
     int kind, f, item;
     p.sch.decode(k, kind, f, item);
+    unsigned t2 = 0xffffffffu;
+    if (threadIdx.x == 0) {
+      t2 = (*(volatile unsigned*)&p.ctr->abort) ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
+      if (t1 < total) prefetch_row_input<NX, NY>(p, t1);
+    }
     const bool ok = kind == 0 ? row_item<NX, NY, FW>(p, f, item, smem, &s_flag)
                               : col_item<NY, FW>(p, f, item, smem, &s_flag);
     if (!ok) break;
-    if (threadIdx.x == 0) s_ticket = next;  // every thread read s_ticket before the item's barriers
+    if (threadIdx.x == 0) {  // every thread read s_ticket before the item's barriers
+      s_ticket = t1;
+      t1 = t2;
+    }
   }
 }
 
