@@ -1,8 +1,14 @@
 // Lateral stage: chromatic rescale (Eq. 5) + Fresnel transform (Eq. 6) of every
-// frame of a sweep, as one persistent kernel.
+// frame of a sweep, as one persistent, warp-specialised kernel.
 //
-// Work items, taken from a device ticket counter in the order LateralSchedule
-// defines:
+// Each CTA has one producer warp and eight consumer warps.  The producer takes
+// work items from a device ticket counter (in the order LateralSchedule
+// defines), waits until an item's inputs are ready, and copies them into one of
+// two shared-memory stage buffers with the Tensor Memory Accelerator (a 1D bulk
+// copy of the uint16 input rows, or 2D tensor copies of an L2 scratch column
+// band), handing the item over through an mbarrier.  Consumers only compute; when
+// they are done with an item they arrive on a second mbarrier, and the producer
+// then publishes the item's completion to the other CTAs.  Items:
 //  * row item (frame f, band of rows): stage the input rows the band needs in
 //    shared memory as float, resample them with the frame's separable linear-
 //    interpolation taps, multiply by the input chirp (centring phase folded in),
@@ -16,77 +22,133 @@
 // The scratch ring holds `slots` frames, so the row-transformed frames never
 // leave L2: only the uint16 input is read from HBM and only the windowed
 // complex hologram is written to it.
-#include <cstdio>
+#include <cuda.h>
 
 #include "fft_common.cuh"
 
 namespace ssoct {
 namespace {
 
-constexpr unsigned kSpinLimit = 1u << 24;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+constexpr int kCtaThreads = kThreads + 32;            // 8 consumer warps + 1 producer warp
+constexpr unsigned long long kProducerWaitNs = 2000000000ull;   // 2 s
+constexpr unsigned long long kConsumerWaitNs = 4000000000ull;   // longer: the producer gives up first
+enum : int { kRowItem = 0, kColItem = 1, kEndItem = 2 };
 
-// One thread waits until *ctr >= target.  Bounded: on timeout it records
-// kErrTimeout, raises the abort flag and returns false; it also returns false
-// as soon as another CTA raised the abort flag.
-__device__ bool wait_counter(const unsigned* ctr, unsigned target, Counters* c) {
-  if (ld_acquire_gpu(ctr) >= target) return true;
+struct Desc {
+  int kind, f, item, jlo, nrows;
+};
+
+// ---------------------------------------------------------------- mbarrier / TMA
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for an mbarrier phase; on timeout records kErrTimeout and aborts.
+__device__ bool mbar_wait(uint64_t* b, unsigned parity, Counters* c, unsigned long long limit_ns) {
+  if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
-  for (unsigned it = 0;; ++it) {
-    if (ld_acquire_gpu(ctr) >= target) return true;
-    if (*(volatile unsigned*)&c->abort) return false;
-    if (it > kSpinLimit || global_timer_ns() - t0 > kWaitNs) {
+  for (;;) {
+    if (mbar_try(b, parity)) return true;
+    if (global_timer_ns() - t0 > limit_ns) {
       atomicCAS(&c->err, 0u, kErrTimeout);
       atomicExch(&c->abort, 1u);
       return false;
     }
-    __nanosleep(128);
   }
 }
+// 1D bulk copy global -> shared, completion counted on an mbarrier.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// 2D tiled tensor copy global -> shared (box as set in the tensor map).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Barrier of the consumer warps only (named barrier 1); returns the OR of `v`.
+__device__ __forceinline__ bool consumers_sync_or(bool v) {
+  unsigned r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+               : "=r"(r)
+               : "r"((unsigned)v), "n"(kThreads)
+               : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
 
-// Row item: rows [item*RPI, item*RPI + RPI) of frame f.
+// ---------------------------------------------------------------- consumer work
+
+// Row item: rows [item*RPI, item*RPI + RPI) of frame d.f; `in` holds input rows
+// jlo .. jlo + nrows - 1 (uint16) copied by the producer.
 template <int NX, int NY, bool FW>
-__device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item, unsigned char* smem,
-                                         int* s_flag) {
+__device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, const uint16_t* in,
+                                         unsigned char* xb) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
   constexpr int RPI = kThreads / N1;
   constexpr int LD = N1 + 1;  // padded exchange row: conflict-free transposed reads
+  constexpr int SP = NX + 2 * kStagePad;
   const int tid = threadIdx.x;
   const int r = tid / N1;
   const int j1 = tid % N1;
-  const int row0 = item * RPI;
-  const int y = row0 + r;
-  const Tap* yt = p.ytab + (size_t)f * NY;
-  const int jlo = yt[row0].base;
-  const int jhi = yt[row0 + RPI - 1].base + 1;
-  const int nrows = jhi - jlo + 1;
-  const int fr = (p.ring_start + f) % p.nl;
-  const unsigned long long pol_first = policy_evict_first();
-  const unsigned long long pol_last = policy_evict_last();
-  // 1. stage input rows jlo..jhi as float, each row padded with zeros on both
-  //    sides so that taps outside the frame read 0 (8 pixels per 16-byte load)
-  constexpr int SP = NX + 2 * kStagePad;
-  float* stage = reinterpret_cast<float*>(smem);
+  const int f = d.f;
+  const int y = d.item * RPI + r;
+  // 1. uint16 rows -> float rows padded with zeros on both sides, so that taps
+  //    outside the frame read 0
+  float* stage = reinterpret_cast<float*>(xb);
   {
-    const uint4* s4 = reinterpret_cast<const uint4*>(p.frames + ((size_t)fr * NY + jlo) * NX);
-    const int nvec = nrows * (NX / 8);
+    const uint4* s4 = reinterpret_cast<const uint4*>(in);
+    const int nvec = d.nrows * (NX / 8);
     for (int i = tid; i < nvec; i += kThreads) {
-      const uint4 v = ld_nc_hint(s4 + i, pol_first);
+      const uint4 v = s4[i];
       float4* d4 = reinterpret_cast<float4*>(stage + (i / (NX / 8)) * SP + kStagePad + (i % (NX / 8)) * 8);
       d4[0] = make_float4(u16lo_to_f(v.x), u16hi_to_f(v.x), u16lo_to_f(v.y), u16hi_to_f(v.y));
       d4[1] = make_float4(u16lo_to_f(v.z), u16hi_to_f(v.z), u16lo_to_f(v.w), u16hi_to_f(v.w));
     }
-    for (int i = tid; i < nrows; i += kThreads) {
+    for (int i = tid; i < d.nrows; i += kThreads) {
       stage[i * SP + kStagePad - 1] = 0.f;
       stage[i * SP + kStagePad + NX] = 0.f;
     }
   }
-  __syncthreads();
+  consumers_sync();
   // 2. Eq. 5 resample x input chirp, elements n = j1 + N1 * j2 of row y
   float2 a[N2];
   {
-    const Tap ty = yt[y];
-    const float* r0 = stage + (ty.base - jlo) * SP + kStagePad;
+    const Tap ty = p.ytab[(size_t)f * NY + y];
+    const float* r0 = stage + (ty.base - d.jlo) * SP + kStagePad;
     const float* r1 = r0 + SP;
     const float4* xt = reinterpret_cast<const float4*>(p.xtab + (size_t)f * NX);
 #pragma unroll
@@ -101,23 +163,16 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
       a[j2] = make_float2(v * t.z, v * t.w);
     }
   }
-  // 3. row DFT (+ sign of Eq. 6), first factor in registers
+  // 3. row DFT (+ sign of Eq. 6): N2-point DFT in registers, twiddle with the
+  //    row's y chirp folded in, transpose through shared memory, N1-point DFTs
   Dft<N2, 1>::template run<1, 0>(a);
   {
     const float2 cyv = ldg2(p.cy + y);
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(ldg2(p.twx + k2 * N1 + j1), cyv));
   }
-  // the scratch slot of frame f must be free (the columns of frame f - slots
-  // done); thread 0 checks before the barrier that retires the staging rows
-  if (tid == 0) {
-    *s_flag = 0;
-    if (f >= p.sch.slots)
-      *s_flag = wait_counter(p.cols_done + (f - p.sch.slots), (unsigned)p.sch.n_col, p.ctr) ? 0 : 1;
-  }
-  __syncthreads();  // staging rows are dead: the exchange buffer reuses them
-  if (*s_flag) return false;
-  float2* exr = reinterpret_cast<float2*>(smem) + r * (N2 * LD);
+  consumers_sync();  // the float rows are dead: the exchange reuses them
+  float2* exr = reinterpret_cast<float2*>(xb) + r * (N2 * LD);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) exr[k2 * LD + j1] = a[k2];
   __syncwarp();  // a row's N1 threads lie in one warp
@@ -128,6 +183,8 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = exr[k2 * LD + jj];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
+  // 4. window columns into the scratch slot of frame f (the producer checked it is free)
+  const unsigned long long pol_last = policy_evict_last();
   float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -142,15 +199,13 @@ __device__ __forceinline__ bool row_item(const LateralParams& p, int f, int item
       }
     }
   });
-  __syncthreads();
-  if (tid == 0) red_release_gpu(p.rows_done + f, 1u);
-  return true;
 }
 
-// Column item: window columns [item*BC, item*BC + BC) of frame f.
+// Column item: window columns [item*BC, item*BC + BC) of frame d.f; `tile` holds
+// the band [NY][BC] (complex) copied from the scratch slot by the producer.
 template <int NY, bool FW>
-__device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item, unsigned char* smem,
-                                         int* s_flag) {
+__device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, const float2* tile,
+                                         unsigned char* xb) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
   // padded k2 block: the 16 lanes of a half-warp read 16/BC k2 blocks at once,
@@ -159,23 +214,16 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
   const int tid = threadIdx.x;
   const int b = tid % BC;
   const int j1 = tid / BC;
-  if (tid == 0) *s_flag = wait_counter(p.rows_done + f, (unsigned)p.sch.n_row, p.ctr) ? 0 : 1;
-  __syncthreads();
-  if (*s_flag) return false;
-  const unsigned long long pol_first = policy_evict_first();
-  const unsigned long long pol_last = policy_evict_last();
-  const int c0 = item * BC;
-  const float2* src = p.scratch + (size_t)(f % p.sch.slots) * NY * p.wxp + c0 + b;
   float2 a[N2];
 #pragma unroll
-  for (int j2 = 0; j2 < N2; ++j2) a[j2] = ld_cg_hint(src + (size_t)(j1 + N1 * j2) * p.wxp, pol_last);
+  for (int j2 = 0; j2 < N2; ++j2) a[j2] = tile[(j1 + N1 * j2) * BC + b];
   Dft<N2, 1>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(p.twy + k2 * N1 + j1));
-  float2* ex = reinterpret_cast<float2*>(smem);
+  float2* ex = reinterpret_cast<float2*>(xb);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) ex[k2 * KP + j1 * BC + b] = a[k2];
-  __syncthreads();
+  consumers_sync();
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
@@ -183,9 +231,10 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[k2 * KP + jj * BC + b];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  const int kxw = c0 + b;
+  const int kxw = d.item * BC + b;
   if (kxw < p.wx) {
-    float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)f * kTile + (kxw % kTile);
+    const unsigned long long pol_first = policy_evict_first();
+    float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)d.f * kTile + (kxw % kTile);
     const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
     static_for<0, N2 / N1>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -201,90 +250,205 @@ __device__ __forceinline__ bool col_item(const LateralParams& p, int f, int item
       }
     });
   }
-  __syncthreads();
-  if (tid == 0) red_release_gpu(p.cols_done + f, 1u);
-  return true;
 }
 
-// L2 prefetch of the input rows a row item will stage (nothing for a column item).
+// ---------------------------------------------------------------- producer
+
+// Producer warp, one thread.  Buffer b holds at most one item; an item is
+// "busy" from its hand-over until the consumers arrive on done[b], at which
+// point its completion is published to other CTAs (red.release after the
+// mbarrier's acquire, so the consumers' stores are visible first).  Every wait
+// keeps publishing finished items, so a CTA never holds back a completion that
+// another CTA (or its own next item) is waiting for.
 template <int NX, int NY>
-__device__ __forceinline__ void prefetch_row_input(const LateralParams& p, unsigned t) {
-  int kind, f, item;
-  p.sch.decode(t, kind, f, item);
-  if (kind != 0) return;
+__device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64_t* full_bar, uint64_t* done_bar,
+                         Desc* desc, unsigned char* stage0) {
   constexpr int RPI = kThreads / Split<NX>::N1;
-  const Tap* yt = p.ytab + (size_t)f * NY;
-  const int jlo = yt[item * RPI].base;
-  const int jhi = yt[item * RPI + RPI - 1].base + 1;
-  const int fr = (p.ring_start + f) % p.nl;
-  prefetch_l2_bulk(p.frames + ((size_t)fr * NY + jlo) * NX, (unsigned)((jhi - jlo + 1) * NX * sizeof(uint16_t)));
+  constexpr int BC = kThreads / Split<NY>::N1;
+  constexpr int BOX_ROWS = NY < 256 ? NY : 256;
+  const long long total = p.sch.total();
+  int busy_kind[2] = {-1, -1}, busy_f[2] = {0, 0};
+  unsigned phase[2] = {0u, 0u};
+  auto service = [&]() {
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+      if (busy_kind[b] >= 0 && mbar_test(&done_bar[b], phase[b])) {
+        red_release_gpu((busy_kind[b] == kRowItem ? p.rows_done : p.cols_done) + busy_f[b], 1u);
+        busy_kind[b] = -1;
+        phase[b] ^= 1u;
+      }
+  };
+  auto give_up = [&]() {
+    atomicCAS(&p.ctr->err, 0u, kErrTimeout);
+    atomicExch(&p.ctr->abort, 1u);
+  };
+  bool failed = false;
+  for (int s = 0;; ++s) {
+    const int b = s & 1;
+    unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
+    // 1. the buffer's previous item must be finished
+    if (busy_kind[b] >= 0) {
+      const unsigned long long t0 = global_timer_ns();
+      while (busy_kind[b] >= 0) {
+        service();
+        if (busy_kind[b] >= 0 && global_timer_ns() - t0 > kProducerWaitNs) {
+          give_up();
+          failed = true;
+          break;
+        }
+      }
+    }
+    // 2. next ticket
+    unsigned t = 0xffffffffu;
+    if (!failed && !*(volatile unsigned*)&p.ctr->abort) t = atomicAdd(&p.ctr->ticket, 1u);
+    int kind = kEndItem, f = 0, item = 0;
+    if (t < total) p.sch.decode(t, kind, f, item);
+    // 3. its dependency: a column item needs every row item of its frame; a row
+    //    item needs the columns of the frame whose scratch slot it reuses
+    if (kind != kEndItem) {
+      const unsigned* dep = nullptr;
+      unsigned target = 0;
+      if (kind == kColItem) {
+        dep = p.rows_done + f;
+        target = (unsigned)p.sch.n_row;
+      } else if (f >= p.sch.slots) {
+        dep = p.cols_done + (f - p.sch.slots);
+        target = (unsigned)p.sch.n_col;
+      }
+      if (dep && ld_acquire_gpu(dep) < target) {
+        const unsigned long long t0 = global_timer_ns();
+        while (ld_acquire_gpu(dep) < target) {
+          service();
+          if (*(volatile unsigned*)&p.ctr->abort || global_timer_ns() - t0 > kProducerWaitNs) {
+            give_up();
+            kind = kEndItem;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+    }
+    // 4. hand over
+    if (kind == kEndItem) {
+      Desc d{kEndItem, 0, 0, 0, 0};
+      desc[b] = d;
+      mbar_arrive(&full_bar[b]);
+      break;
+    }
+    Desc d{kind, f, item, 0, 0};
+    if (kind == kRowItem) {
+      const Tap* yt = p.ytab + (size_t)f * NY;
+      d.jlo = yt[item * RPI].base;
+      d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
+      const unsigned bytes = (unsigned)(d.nrows * NX * sizeof(uint16_t));
+      desc[b] = d;
+      mbar_arrive_tx(&full_bar[b], bytes);
+      const int fr = (p.ring_start + f) % p.nl;
+      tma_load_1d(buf, p.frames + ((size_t)fr * NY + d.jlo) * NX, bytes, &full_bar[b]);
+    } else {
+      desc[b] = d;
+      mbar_arrive_tx(&full_bar[b], (unsigned)(NY * BC * sizeof(float2)));
+      const int x = 2 * item * BC;
+      const int y0 = (f % p.sch.slots) * NY;
+#pragma unroll
+      for (int i = 0; i < NY / BOX_ROWS; ++i)
+        tma_load_2d(buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), tmap, x, y0 + i * BOX_ROWS, &full_bar[b]);
+    }
+    busy_kind[b] = kind;
+    busy_f[b] = f;
+  }
+  // drain: publish what is still in flight
+  const unsigned long long t0 = global_timer_ns();
+  while (busy_kind[0] >= 0 || busy_kind[1] >= 0) {
+    service();
+    if ((busy_kind[0] >= 0 || busy_kind[1] >= 0) && global_timer_ns() - t0 > kProducerWaitNs) {
+      give_up();
+      break;
+    }
+  }
 }
 
 template <int NX, int NY, bool FW>
-__global__ void __launch_bounds__(kThreads, 2) lateral_kernel(const __grid_constant__ LateralParams p) {
+__global__ void __launch_bounds__(kCtaThreads, 1)
+    lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned s_ticket;
-  __shared__ int s_flag;
-  const long long total = p.sch.total();
-  // Thread 0 keeps the ticket after the current one (t1) in hand and takes the
-  // one after that while the current item runs, so the atomic round trip hides
-  // behind the item; t1's input rows are prefetched into L2 meanwhile.  A CTA
-  // holds at most two unstarted tickets, and the lowest unfinished ticket is
-  // always the one its CTA is working on, so the queue still drains.
-  unsigned t1 = 0xffffffffu;
-  if (threadIdx.x == 0) {
-    s_ticket = atomicAdd(&p.ctr->ticket, 1u);
-    t1 = atomicAdd(&p.ctr->ticket, 1u);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full_bar[2];
+  __shared__ __align__(8) uint64_t done_bar[2];
+  __shared__ Desc desc[2];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&full_bar[0], 1);
+    mbar_init(&full_bar[1], 1);
+    mbar_init(&done_bar[0], kThreads);
+    mbar_init(&done_bar[1], kThreads);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (;;) {
-    __syncthreads();
-    const long long k = s_ticket;
-    if (k >= total) break;
-    int kind, f, item;
-    p.sch.decode(k, kind, f, item);
-    unsigned t2 = 0xffffffffu;
-    if (threadIdx.x == 0) {
-      t2 = (*(volatile unsigned*)&p.ctr->abort) ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-      if (t1 < total) prefetch_row_input<NX, NY>(p, t1);
-    }
-    const bool ok = kind == 0 ? row_item<NX, NY, FW>(p, f, item, smem, &s_flag)
-                              : col_item<NY, FW>(p, f, item, smem, &s_flag);
-    if (!ok) break;
-    if (threadIdx.x == 0) {  // every thread read s_ticket before the item's barriers
-      s_ticket = t1;
-      t1 = t2;
-    }
+  __syncthreads();
+  unsigned char* stage0 = smem;
+  unsigned char* xb = smem + 2 * (size_t)p.stage_bytes;
+  if (tid >= kThreads) {
+    if (tid == kThreads) producer<NX, NY>(p, &tmap, full_bar, done_bar, desc, stage0);
+    return;
   }
+  for (int s = 0;; ++s) {
+    const int b = s & 1;
+    const bool ok = mbar_wait(&full_bar[b], (unsigned)((s >> 1) & 1), p.ctr, kConsumerWaitNs);
+    // all consumers agree, and the previous item's readers of xb are done
+    if (consumers_sync_or(!ok)) break;
+    const Desc d = desc[b];
+    if (d.kind == kEndItem) break;
+    const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
+    if (d.kind == kRowItem)
+      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb);
+    else
+      col_item<NY, FW>(p, d, reinterpret_cast<const float2*>(buf), xb);
+    mbar_arrive(&done_bar[b]);
+  }
+}
+
+// Shared memory: two stage buffers (input rows of a row item, or a column band)
+// and one exchange buffer (float rows / row transpose / column transpose).
+template <int NX, int NY>
+void smem_layout(const Plan& p, size_t& stage_bytes, size_t& total) {
+  constexpr int N1x = Split<NX>::N1, N2x = Split<NX>::N2;
+  constexpr int N1y = Split<NY>::N1, N2y = Split<NY>::N2;
+  constexpr int BCy = kThreads / N1y;
+  const size_t in_rows = (size_t)p.stage_rows * NX * sizeof(uint16_t);
+  const size_t in_cols = (size_t)NY * BCy * sizeof(float2);
+  stage_bytes = ((in_rows > in_cols ? in_rows : in_cols) + 1023) / 1024 * 1024;
+  const size_t fl = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
+  const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
+  const size_t cols = (size_t)N2y * (N1y * BCy + (BCy < 16 ? BCy : 0)) * sizeof(float2);
+  size_t x = fl > rows ? fl : rows;
+  x = x > cols ? x : cols;
+  total = 2 * stage_bytes + x;
 }
 
 template <int NX, int NY>
 size_t smem_for(const Plan& p) {
-  constexpr int N1x = Split<NX>::N1, N2x = Split<NX>::N2;
-  constexpr int N1y = Split<NY>::N1;
-  constexpr int N2y = Split<NY>::N2;
-  const size_t stage = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
-  const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
-  constexpr int BCy = kThreads / N1y;
-  const size_t cols = (size_t)N2y * (N1y * BCy + (BCy < 16 ? BCy : 0)) * sizeof(float2);
-  size_t m = stage > rows ? stage : rows;
-  return m > cols ? m : cols;
+  size_t sb, total;
+  smem_layout<NX, NY>(p, sb, total);
+  return total;
 }
 
 template <int NX, int NY, bool FW>
-cudaError_t launch_fw(const Plan& p, const LateralParams& lp, cudaStream_t s) {
-  const size_t smem = smem_for<NX, NY>(p);
+cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, cudaStream_t s) {
+  size_t sb, smem;
+  smem_layout<NX, NY>(p, sb, smem);
+  LateralParams lp = lp_in;
+  lp.stage_bytes = (int)sb;
   cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  long long total = lp.sch.total();
+  const long long total = lp.sch.total();
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY, FW>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY, FW>, kCtaThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = (p.num_sms > 0 ? p.num_sms : 1) * per_sm;
   if (grid > total) grid = (int)total;
-  lateral_kernel<NX, NY, FW><<<grid, kThreads, smem, s>>>(lp);
+  lateral_kernel<NX, NY, FW><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(p.tmap));
   return cudaGetLastError();
 }
 
@@ -312,6 +476,8 @@ size_t lateral_smem_bytes(const Plan& p) {
 #undef X
   return 0;
 }
+
+int lateral_col_band(int ny) { return kThreads / split_n1(ny); }
 
 cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s) {
 #define X(a, b) if (p.nx == a && p.ny == b) return launch<a, b>(p, lp, s);

@@ -123,6 +123,7 @@ struct LateralParams {
   unsigned* cols_done;     // [nl]
   LateralSchedule sch;
   int stage_rows;          // input rows staged per row item (max over items)
+  int stage_bytes;         // bytes of one shared-memory stage buffer (set at launch)
 };
 
 struct AxialParams {
@@ -170,6 +171,7 @@ struct Plan {
   char* ws = nullptr;
   int device = -1;
   int num_sms = 0;
+  alignas(64) unsigned char tmap[128];  // CUtensorMap of the scratch ring (column bands)
   // frame ring state
   long long pushed = 0;     // frames in the current gate (capped at nl)
   int ring_head = 0;        // next ring slot to write
@@ -189,5 +191,7 @@ bool lateral_supported(int nx, int ny);
 bool axial_supported(int nl);
 // Dynamic shared memory of the lateral kernel for a plan (bytes).
 size_t lateral_smem_bytes(const Plan& p);
+// Columns per column item of the lateral kernel for a column length ny.
+int lateral_col_band(int ny);
 
 }  // namespace ssoct

@@ -5,6 +5,9 @@
 #include <cstring>
 #include <new>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "ssoct_internal.h"
 
 using namespace ssoct;
@@ -113,6 +116,36 @@ std::vector<float2> twiddles(int n, int n1, int n2, int sign) {
       v[(size_t)k2 * n1 + j1] = cis_pi(sign * 2.0 * (double)e / n);
     }
   return v;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+// Tensor map over the scratch ring seen as float32 [slots * ny][2 * wxp]; one
+// box is a column band of the lateral kernel (2 * band floats x min(ny, 256) rows).
+bool encode_scratch_map(Plan& p) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int band = lateral_col_band(p.ny);
+  cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.sch.slots * p.ny};
+  cuuint64_t strides[1] = {(cuuint64_t)2 * p.wxp * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)(p.ny < 256 ? p.ny : 256)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(p.tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.ws + p.off_scratch,
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -308,6 +341,10 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
   e = cudaMemset(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl);
   if (e != cudaSuccess) return cuda_fail(&p, e, "counter reset");
   p.ws = ws;
+  if (!encode_scratch_map(p)) {
+    p.ws = nullptr;
+    return fail(&p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the scratch ring");
+  }
   p.pushed = 0;
   p.ring_head = 0;
   p.next_seq = -1;
