@@ -112,11 +112,18 @@ __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;
 
 // ---------------------------------------------------------------- consumer work
 
+// A row item's stage buffer: nrows uint16 input rows, then (16-byte aligned) the
+// frame's NX x taps (TapX, 16 bytes each).
+template <int NX>
+__host__ __device__ constexpr int taps_offset_elems(int nrows) {
+  return (nrows * NX + 7) / 8 * 8;  // in uint16 elements; NX >= 64 keeps it 16-byte aligned
+}
+
 // Row item: rows [item*RPI, item*RPI + RPI) of frame d.f; `in` holds input rows
 // jlo .. jlo + nrows - 1 (uint16) copied by the producer.
 template <int NX, int NY, bool FW>
 __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, const uint16_t* in,
-                                         unsigned char* xb) {
+                                         unsigned char* xb, const float2* twx) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
   constexpr int RPI = kThreads / N1;
   constexpr int LD = N1 + 1;  // padded exchange row: conflict-free transposed reads
@@ -150,11 +157,12 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
     const Tap ty = p.ytab[(size_t)f * NY + y];
     const float* r0 = stage + (ty.base - d.jlo) * SP + kStagePad;
     const float* r1 = r0 + SP;
-    const float4* xt = reinterpret_cast<const float4*>(p.xtab + (size_t)f * NX);
+    // the frame's x taps follow the input rows in the stage buffer
+    const float4* xt = reinterpret_cast<const float4*>(in + taps_offset_elems<NX>(d.nrows));
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) {
       const int n = j1 + N1 * j2;
-      const float4 t = __ldg(xt + n);
+      const float4 t = xt[n];
       const int bx = __float_as_int(t.x);
       const float a0 = r0[bx], a1 = r0[bx + 1], b0 = r1[bx], b1 = r1[bx + 1];
       const float v0 = fmaf(t.y, a1 - a0, a0);
@@ -169,7 +177,7 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   {
     const float2 cyv = ldg2(p.cy + y);
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(ldg2(p.twx + k2 * N1 + j1), cyv));
+    for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
   }
   consumers_sync();  // the float rows are dead: the exchange reuses them
   float2* exr = reinterpret_cast<float2*>(xb) + r * (N2 * LD);
@@ -205,7 +213,7 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
 // the band [NY][BC] (complex) copied from the scratch slot by the producer.
 template <int NY, bool FW>
 __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, const float2* tile,
-                                         unsigned char* xb) {
+                                         unsigned char* xb, const float2* twy) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
   // padded k2 block: the 16 lanes of a half-warp read 16/BC k2 blocks at once,
@@ -219,7 +227,7 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = tile[(j1 + N1 * j2) * BC + b];
   Dft<N2, 1>::template run<1, 0>(a);
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(p.twy + k2 * N1 + j1));
+  for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], twy[k2 * N1 + j1]);
   float2* ex = reinterpret_cast<float2*>(xb);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) ex[k2 * KP + j1 * BC + b] = a[k2];
@@ -341,10 +349,13 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
       d.jlo = yt[item * RPI].base;
       d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
       const unsigned bytes = (unsigned)(d.nrows * NX * sizeof(uint16_t));
+      const unsigned tap_off = (unsigned)(taps_offset_elems<NX>(d.nrows) * sizeof(uint16_t));
+      const unsigned tap_bytes = (unsigned)(NX * sizeof(TapX));
       desc[b] = d;
-      mbar_arrive_tx(&full_bar[b], bytes);
+      mbar_arrive_tx(&full_bar[b], bytes + tap_bytes);
       const int fr = (p.ring_start + f) % p.nl;
       tma_load_1d(buf, p.frames + ((size_t)fr * NY + d.jlo) * NX, bytes, &full_bar[b]);
+      tma_load_1d(buf + tap_off, p.xtab + (size_t)f * NX, tap_bytes, &full_bar[b]);
     } else {
       desc[b] = d;
       mbar_arrive_tx(&full_bar[b], (unsigned)(NY * BC * sizeof(float2)));
@@ -387,10 +398,15 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   __syncthreads();
   unsigned char* stage0 = smem;
   unsigned char* xb = smem + 2 * (size_t)p.stage_bytes;
+  float2* twx = reinterpret_cast<float2*>(xb + p.xbuf_bytes);
+  float2* twy = twx + NX;
   if (tid >= kThreads) {
     if (tid == kThreads) producer<NX, NY>(p, &tmap, full_bar, done_bar, desc, stage0);
     return;
   }
+  for (int i = tid; i < NX; i += kThreads) twx[i] = ldg2(p.twx + i);
+  for (int i = tid; i < NY; i += kThreads) twy[i] = ldg2(p.twy + i);
+  // (visible to all consumers after the first consumers_sync_or below)
   for (int s = 0;; ++s) {
     const int b = s & 1;
     const bool ok = mbar_wait(&full_bar[b], (unsigned)((s >> 1) & 1), p.ctr, kConsumerWaitNs);
@@ -400,9 +416,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     if (d.kind == kEndItem) break;
     const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     if (d.kind == kRowItem)
-      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb);
+      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb, twx);
     else
-      col_item<NY, FW>(p, d, reinterpret_cast<const float2*>(buf), xb);
+      col_item<NY, FW>(p, d, reinterpret_cast<const float2*>(buf), xb, twy);
     mbar_arrive(&done_bar[b]);
   }
 }
@@ -410,11 +426,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
 // Shared memory: two stage buffers (input rows of a row item, or a column band)
 // and one exchange buffer (float rows / row transpose / column transpose).
 template <int NX, int NY>
-void smem_layout(const Plan& p, size_t& stage_bytes, size_t& total) {
+void smem_layout(const Plan& p, size_t& stage_bytes, size_t& xbuf_bytes, size_t& total) {
   constexpr int N1x = Split<NX>::N1, N2x = Split<NX>::N2;
   constexpr int N1y = Split<NY>::N1, N2y = Split<NY>::N2;
   constexpr int BCy = kThreads / N1y;
-  const size_t in_rows = (size_t)p.stage_rows * NX * sizeof(uint16_t);
+  const size_t in_rows = (size_t)taps_offset_elems<NX>(p.stage_rows) * sizeof(uint16_t) + NX * sizeof(TapX);
   const size_t in_cols = (size_t)NY * BCy * sizeof(float2);
   stage_bytes = ((in_rows > in_cols ? in_rows : in_cols) + 1023) / 1024 * 1024;
   const size_t fl = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
@@ -422,22 +438,24 @@ void smem_layout(const Plan& p, size_t& stage_bytes, size_t& total) {
   const size_t cols = (size_t)N2y * (N1y * BCy + (BCy < 16 ? BCy : 0)) * sizeof(float2);
   size_t x = fl > rows ? fl : rows;
   x = x > cols ? x : cols;
-  total = 2 * stage_bytes + x;
+  xbuf_bytes = (x + 15) / 16 * 16;
+  total = 2 * stage_bytes + xbuf_bytes + (size_t)(NX + NY) * sizeof(float2);  // + twiddle tables
 }
 
 template <int NX, int NY>
 size_t smem_for(const Plan& p) {
-  size_t sb, total;
-  smem_layout<NX, NY>(p, sb, total);
+  size_t sb, xb, total;
+  smem_layout<NX, NY>(p, sb, xb, total);
   return total;
 }
 
 template <int NX, int NY, bool FW>
 cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, cudaStream_t s) {
-  size_t sb, smem;
-  smem_layout<NX, NY>(p, sb, smem);
+  size_t sb, xbb, smem;
+  smem_layout<NX, NY>(p, sb, xbb, smem);
   LateralParams lp = lp_in;
   lp.stage_bytes = (int)sb;
+  lp.xbuf_bytes = (int)xbb;
   cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

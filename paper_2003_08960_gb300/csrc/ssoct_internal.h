@@ -124,6 +124,7 @@ struct LateralParams {
   LateralSchedule sch;
   int stage_rows;          // input rows staged per row item (max over items)
   int stage_bytes;         // bytes of one shared-memory stage buffer (set at launch)
+  int xbuf_bytes;          // bytes of the shared-memory exchange buffer (set at launch)
 };
 
 struct AxialParams {
