@@ -290,28 +290,22 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
     atomicExch(&p.ctr->abort, 1u);
   };
-  bool failed = false;
+  // The producer prepares item s (ticket, dependency, descriptor) while the
+  // consumers still hold both buffers, and only the copy issue waits for buffer
+  // s & 1 to come free.  The ticket after it is requested right away.  A CTA thus
+  // holds at most two unstarted tickets; the lowest unfinished ticket is always
+  // the one its CTA is working on (or has handed over), so the queue drains.
+  unsigned t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
   for (int s = 0;; ++s) {
     const int b = s & 1;
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
-    // 1. the buffer's previous item must be finished
-    if (busy_kind[b] >= 0) {
-      const unsigned long long t0 = global_timer_ns();
-      while (busy_kind[b] >= 0) {
-        service();
-        if (busy_kind[b] >= 0 && global_timer_ns() - t0 > kProducerWaitNs) {
-          give_up();
-          failed = true;
-          break;
-        }
-      }
-    }
-    // 2. next ticket
-    unsigned t = 0xffffffffu;
-    if (!failed && !*(volatile unsigned*)&p.ctr->abort) t = atomicAdd(&p.ctr->ticket, 1u);
+    const unsigned t = t_next;
     int kind = kEndItem, f = 0, item = 0;
-    if (t < total) p.sch.decode(t, kind, f, item);
-    // 3. its dependency: a column item needs every row item of its frame; a row
+    if (t < total) {
+      p.sch.decode(t, kind, f, item);
+      t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
+    }
+    // 1. its dependency: a column item needs every row item of its frame; a row
     //    item needs the columns of the frame whose scratch slot it reuses
     if (kind != kEndItem) {
       const unsigned* dep = nullptr;
@@ -336,18 +330,31 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
         }
       }
     }
-    // 4. hand over
-    if (kind == kEndItem) {
-      Desc d{kEndItem, 0, 0, 0, 0};
-      desc[b] = d;
-      mbar_arrive(&full_bar[b]);
-      break;
-    }
     Desc d{kind, f, item, 0, 0};
     if (kind == kRowItem) {
       const Tap* yt = p.ytab + (size_t)f * NY;
       d.jlo = yt[item * RPI].base;
       d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
+    }
+    // 2. the buffer's previous item must be finished
+    if (busy_kind[b] >= 0) {
+      const unsigned long long t0 = global_timer_ns();
+      while (busy_kind[b] >= 0) {
+        service();
+        if (busy_kind[b] >= 0 && global_timer_ns() - t0 > kProducerWaitNs) {
+          give_up();
+          kind = kEndItem;  // the buffer's old item is lost; consumers still get an end mark
+          break;
+        }
+      }
+    }
+    // 3. hand over
+    if (kind == kEndItem) {
+      desc[b] = Desc{kEndItem, 0, 0, 0, 0};
+      mbar_arrive(&full_bar[b]);
+      break;
+    }
+    if (kind == kRowItem) {
       const unsigned bytes = (unsigned)(d.nrows * NX * sizeof(uint16_t));
       const unsigned tap_off = (unsigned)(taps_offset_elems<NX>(d.nrows) * sizeof(uint16_t));
       const unsigned tap_bytes = (unsigned)(NX * sizeof(TapX));
