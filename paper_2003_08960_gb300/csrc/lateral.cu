@@ -113,10 +113,16 @@ __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;
 // ---------------------------------------------------------------- consumer work
 
 // A row item's stage buffer: nrows uint16 input rows, then (16-byte aligned) the
-// frame's NX x taps (TapX, 16 bytes each).
+// frame's NX x taps (TapX, 16 bytes each), the RPI y taps of its rows (Tap) and
+// the RPI y chirps of its rows (float2).
 template <int NX>
 __host__ __device__ constexpr int taps_offset_elems(int nrows) {
   return (nrows * NX + 7) / 8 * 8;  // in uint16 elements; NX >= 64 keeps it 16-byte aligned
+}
+template <int NX>
+__host__ __device__ constexpr size_t row_stage_bytes(int nrows) {
+  return (size_t)taps_offset_elems<NX>(nrows) * 2 + (size_t)NX * sizeof(TapX) +
+         (size_t)(kThreads / split_n1(NX)) * (sizeof(Tap) + sizeof(float2));
 }
 
 // Row item: rows [item*RPI, item*RPI + RPI) of frame d.f; `in` holds input rows
@@ -152,13 +158,15 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   }
   consumers_sync();
   // 2. Eq. 5 resample x input chirp, elements n = j1 + N1 * j2 of row y
+  const TapX* xtaps = reinterpret_cast<const TapX*>(in + taps_offset_elems<NX>(d.nrows));
+  const Tap* ytaps = reinterpret_cast<const Tap*>(xtaps + NX);
+  const float2* ychirp = reinterpret_cast<const float2*>(ytaps + RPI);
   float2 a[N2];
   {
-    const Tap ty = p.ytab[(size_t)f * NY + y];
+    const Tap ty = ytaps[r];
     const float* r0 = stage + (ty.base - d.jlo) * SP + kStagePad;
     const float* r1 = r0 + SP;
-    // the frame's x taps follow the input rows in the stage buffer
-    const float4* xt = reinterpret_cast<const float4*>(in + taps_offset_elems<NX>(d.nrows));
+    const float4* xt = reinterpret_cast<const float4*>(xtaps);
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) {
       const int n = j1 + N1 * j2;
@@ -175,7 +183,7 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   //    row's y chirp folded in, transpose through shared memory, N1-point DFTs
   Dft<N2, 1>::template run<1, 0>(a);
   {
-    const float2 cyv = ldg2(p.cy + y);
+    const float2 cyv = ychirp[r];
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
   }
@@ -358,11 +366,15 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
       const unsigned bytes = (unsigned)(d.nrows * NX * sizeof(uint16_t));
       const unsigned tap_off = (unsigned)(taps_offset_elems<NX>(d.nrows) * sizeof(uint16_t));
       const unsigned tap_bytes = (unsigned)(NX * sizeof(TapX));
+      const unsigned yt_bytes = (unsigned)(RPI * sizeof(Tap));
+      const unsigned cy_bytes = (unsigned)(RPI * sizeof(float2));
       desc[b] = d;
-      mbar_arrive_tx(&full_bar[b], bytes + tap_bytes);
+      mbar_arrive_tx(&full_bar[b], bytes + tap_bytes + yt_bytes + cy_bytes);
       const int fr = (p.ring_start + f) % p.nl;
       tma_load_1d(buf, p.frames + ((size_t)fr * NY + d.jlo) * NX, bytes, &full_bar[b]);
       tma_load_1d(buf + tap_off, p.xtab + (size_t)f * NX, tap_bytes, &full_bar[b]);
+      tma_load_1d(buf + tap_off + tap_bytes, p.ytab + (size_t)f * NY + item * RPI, yt_bytes, &full_bar[b]);
+      tma_load_1d(buf + tap_off + tap_bytes + yt_bytes, p.cy + item * RPI, cy_bytes, &full_bar[b]);
     } else {
       desc[b] = d;
       mbar_arrive_tx(&full_bar[b], (unsigned)(NY * BC * sizeof(float2)));
@@ -437,7 +449,7 @@ void smem_layout(const Plan& p, size_t& stage_bytes, size_t& xbuf_bytes, size_t&
   constexpr int N1x = Split<NX>::N1, N2x = Split<NX>::N2;
   constexpr int N1y = Split<NY>::N1, N2y = Split<NY>::N2;
   constexpr int BCy = kThreads / N1y;
-  const size_t in_rows = (size_t)taps_offset_elems<NX>(p.stage_rows) * sizeof(uint16_t) + NX * sizeof(TapX);
+  const size_t in_rows = row_stage_bytes<NX>(p.stage_rows);
   const size_t in_cols = (size_t)NY * BCy * sizeof(float2);
   stage_bytes = ((in_rows > in_cols ? in_rows : in_cols) + 1023) / 1024 * 1024;
   const size_t fl = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
