@@ -300,19 +300,16 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
   };
   // The producer prepares item s (ticket, dependency, descriptor) while the
   // consumers still hold both buffers, and only the copy issue waits for buffer
-  // s & 1 to come free.  The ticket after it is requested right away.  A CTA thus
-  // holds at most two unstarted tickets; the lowest unfinished ticket is always
-  // the one its CTA is working on (or has handed over), so the queue drains.
+  // s & 1 to come free.  A CTA holds at most one unstarted, unpublished ticket;
+  // the lowest unfinished ticket is always one its CTA is working on or has
+  // handed over, so the queue drains.
   unsigned t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
   for (int s = 0;; ++s) {
     const int b = s & 1;
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     const unsigned t = t_next;
     int kind = kEndItem, f = 0, item = 0;
-    if (t < total) {
-      p.sch.decode(t, kind, f, item);
-      t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-    }
+    if (t < total) p.sch.decode(t, kind, f, item);
     // 1. its dependency: a column item needs every row item of its frame; a row
     //    item needs the columns of the frame whose scratch slot it reuses
     if (kind != kEndItem) {
@@ -386,6 +383,9 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
     }
     busy_kind[b] = kind;
     busy_f[b] = f;
+    // the next ticket, requested once this one is handed over (its round trip
+    // overlaps the wait for the next free buffer)
+    t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
   }
   // drain: publish what is still in flight
   const unsigned long long t0 = global_timer_ns();
