@@ -251,8 +251,10 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.sch.nl = nlambda;
   p.sch.n_row = ny / p.rows_per_item;
   p.sch.n_col = (p.wx + p.cols_per_item - 1) / p.cols_per_item;
-  p.sch.lag = nlambda >= 4 ? 3 : nlambda - 1;
-  p.sch.slots = p.sch.lag + 2;  // a row item then waits on columns two steps back
+  p.sch.lag = nlambda >= 3 ? 2 : nlambda - 1;
+  // a row item of frame f reuses the slot of frame f - slots, whose last column
+  // items were taken four steps earlier: enough slack that the wait is rare
+  p.sch.slots = p.sch.lag + 4;
   // input rows a row item stages: from the first row's base to the last row's base + 1
   int st = 0;
   for (int t = 0; t < nlambda; ++t)
