@@ -138,6 +138,27 @@ SSOCT_API ssoct_status ssoct_reconstruct_volume(ssoct_plan plan, float* vol_dev,
 SSOCT_API ssoct_status ssoct_reconstruct_frames(ssoct_plan plan, const uint16_t* frames_dev,
                                                 float* vol_dev, void* complex_dev, void* stream);
 
+/* Same reconstruction as ssoct_reconstruct_frames, for callers that cannot
+ * allocate device memory: real-time acquisition code that must not allocate
+ * while frames stream in (an allocation can stall the device and drop frames),
+ * or plug-ins whose host application owns the device heap.  The paper has no
+ * counterpart; it is a deployment variant of the same kernels.
+ *   frames_dev, vol_dev, complex_dev: as for ssoct_reconstruct_frames (caller's).
+ * The plan needs no workspace.  All other device memory (tables, the lateral
+ * kernel's L2 scratch ring and counters, the sweep-axis intermediate) comes from
+ * one file-scope device array of 64 MiB that every GPU loading the library keeps
+ * until the process exits.  This call allocates nothing (no cudaMalloc, no
+ * allocating library routine).  Plans whose workspace would exceed 64 MiB get
+ * SSOCT_EUNSUPPORTED with a message saying so (e.g. 256 x 256 x 64 fits,
+ * 512 x 512 x 32 does not).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array and rewrites the tables and zeroes the
+ * counters itself; calls whose work overlaps on the GPU (other streams or host
+ * threads) race on it, so serialise them.  A kernel time-out on this path is not
+ * reported by ssoct_sync. */
+SSOCT_API ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan plan, const uint16_t* frames_dev,
+                                                        float* vol_dev, void* complex_dev, void* stream);
+
 /* The three orthogonal cuts of a volume written by a reconstruct call with this
  * plan (text after Eq. 7; Fig. 5): xy[wy][wx] = P(x, y, z0), xz[nlambda][wx] =
  * P(x, y0, z), yz[nlambda][wy] = P(x0, y, z), coordinates in window pixels and

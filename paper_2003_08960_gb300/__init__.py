@@ -86,6 +86,13 @@ def ssoct_reconstruct_frames(plan, frames_ptr: int, vol_ptr: int, complex_ptr: i
                                                C.c_void_p(complex_ptr or None), C.c_void_p(stream))
 
 
+def ssoct_reconstruct_frames_noalloc(plan, frames_ptr: int, vol_ptr: int, complex_ptr: int, stream: int) -> int:
+    """ssoct_reconstruct_frames without any device allocation (scratch in a fixed
+    64 MiB device array inside the library); the plan needs no workspace."""
+    return _abi.lib().ssoct_reconstruct_frames_noalloc(plan, C.c_void_p(frames_ptr), C.c_void_p(vol_ptr),
+                                                       C.c_void_p(complex_ptr or None), C.c_void_p(stream))
+
+
 def ssoct_get_cuts(plan, vol_ptr: int, x0: int, y0: int, z0: int, xy_ptr: int, xz_ptr: int, yz_ptr: int,
                    stream: int) -> int:
     return _abi.lib().ssoct_get_cuts(plan, C.c_void_p(vol_ptr), x0, y0, z0, C.c_void_p(xy_ptr or None),

@@ -495,6 +495,36 @@ cudaError_t launch(const Plan& p, const LateralParams& lp, cudaStream_t s) {
   return full ? launch_fw<NX, NY, true>(p, lp, s) : launch_fw<NX, NY, false>(p, lp, s);
 }
 
+// Same launch with the scratch-ring tensor map and the SM count given by the
+// caller (used when the scratch lives outside the plan's workspace).
+template <int NX, int NY, bool FW>
+cudaError_t launch_fw_with(const Plan& p, const LateralParams& lp_in, const void* tmap, int num_sms, cudaStream_t s) {
+  size_t sb, xbb, smem;
+  smem_layout<NX, NY>(p, sb, xbb, smem);
+  LateralParams lp = lp_in;
+  lp.stage_bytes = (int)sb;
+  lp.xbuf_bytes = (int)xbb;
+  cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long total = lp.sch.total();
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY, FW>, kCtaThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = (num_sms > 0 ? num_sms : 1) * per_sm;
+  if (grid > total) grid = (int)total;
+  lateral_kernel<NX, NY, FW><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(tmap));
+  return cudaGetLastError();
+}
+
+template <int NX, int NY>
+cudaError_t launch_with(const Plan& p, const LateralParams& lp, const void* tmap, int num_sms, cudaStream_t s) {
+  const bool full = p.x0 == 0 && p.y0 == 0 && p.wx == NX && p.wy == NY;
+  return full ? launch_fw_with<NX, NY, true>(p, lp, tmap, num_sms, s)
+              : launch_fw_with<NX, NY, false>(p, lp, tmap, num_sms, s);
+}
+
 #define SSOCT_LATERAL_SIZES(X) \
   X(64, 64) X(128, 128) X(256, 256) X(512, 512) X(1024, 1024) X(128, 64) X(64, 128)
 
@@ -515,6 +545,14 @@ size_t lateral_smem_bytes(const Plan& p) {
 }
 
 int lateral_col_band(int ny) { return kThreads / split_n1(ny); }
+
+cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap, int num_sms,
+                                cudaStream_t s) {
+#define X(a, b) if (p.nx == a && p.ny == b) return launch_with<a, b>(p, lp, tmap, num_sms, s);
+  SSOCT_LATERAL_SIZES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s) {
 #define X(a, b) if (p.nx == a && p.ny == b) return launch<a, b>(p, lp, s);

@@ -1,0 +1,145 @@
+// Reconstruction without any device allocation, for callers that cannot
+// allocate device memory themselves.
+//
+// Who needs this: acquisition software that reserves all its memory up front and
+// must not allocate while frames stream in (a device allocation can synchronise
+// the device and stall the frame loop, which is exactly the frame drop the
+// acquisition buffering exists to prevent), and plug-ins running inside a host
+// application whose own memory manager owns the device heap and forbids
+// cudaMalloc from third-party code.  Such a caller can still create a plan (host
+// memory only) and pass its own frames and output volume; everything else this
+// path needs lives in one file-scope device array.
+//
+// The array holds the plan's tables, the L2 scratch ring and work counters of
+// the lateral kernel, and the sweep-axis intermediate, laid out exactly like a
+// plan workspace.  It has a fixed size (kNoAllocBytes), and every GPU that loads
+// the library keeps it until the process exits.  All calls share it and it keeps
+// the last call's contents: each call rewrites the tables and zeroes the
+// counters before its kernels run, and calls that overlap on the GPU (different
+// streams, or different host threads) race on it.
+#include <cstdio>
+
+#include "ssoct_internal.h"
+
+namespace ssoct {
+namespace {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;  // 64 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch and SM count, per device (set on first use).
+char* g_scratch_addr[kMaxDevices] = {};
+int g_num_sms[kMaxDevices] = {};
+
+ssoct_status fail(Plan& p, ssoct_status s, const std::string& msg) {
+  p.last_error = msg;
+  return s;
+}
+
+}  // namespace
+}  // namespace ssoct
+
+using namespace ssoct;
+
+extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uint16_t* frames_dev, float* vol_dev,
+                                                         void* complex_dev, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = plan_of(h);
+  if (p.ws_bytes > kNoAllocBytes) {
+    char msg[200];
+    snprintf(msg, sizeof msg,
+             "this plan needs %zu bytes of device scratch; the no-allocation entry point holds at most %zu (64 MiB)",
+             p.ws_bytes, kNoAllocBytes);
+    return fail(p, SSOCT_EUNSUPPORTED, msg);
+  }
+  if (!frames_dev || ((uintptr_t)frames_dev % 16)) return fail(p, SSOCT_EINVAL, "frames NULL or not 16-byte aligned");
+  if (!vol_dev || ((uintptr_t)vol_dev % 16) || ((uintptr_t)complex_dev % 16))
+    return fail(p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(p, SSOCT_EUNSUPPORTED, "device index beyond the no-allocation table");
+  // One-time set-up on this device (the current one): the array's device address.
+  // In host code the name g_noalloc_scratch is only a host-side stand-in, so the
+  // kernels get this address instead.
+  if (!g_scratch_addr[dev]) {
+    char* addr = nullptr;
+    e = cudaGetSymbolAddress((void**)&addr, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+    g_num_sms[dev] = sms;
+    g_scratch_addr[dev] = addr;
+  }
+  char* ws = g_scratch_addr[dev];
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // Tables of this plan (the previous call may have left another plan's), then
+  // zeroed work counters.
+  struct Up {
+    size_t off;
+    const void* src;
+    size_t n;
+  } ups[] = {
+      {p.off_xtab, p.xtab.data(), sizeof(TapX) * p.xtab.size()},
+      {p.off_ytab, p.ytab.data(), sizeof(Tap) * p.ytab.size()},
+      {p.off_cx, p.cx.data(), sizeof(float2) * p.cx.size()},
+      {p.off_cy, p.cy.data(), sizeof(float2) * p.cy.size()},
+      {p.off_ox, p.ox.data(), sizeof(float2) * p.ox.size()},
+      {p.off_oy, p.oy.data(), sizeof(float2) * p.oy.size()},
+      {p.off_twx, p.twx.data(), sizeof(float2) * p.twx.size()},
+      {p.off_twy, p.twy.data(), sizeof(float2) * p.twy.size()},
+      {p.off_twl, p.twl.data(), sizeof(float2) * p.twl.size()},
+  };
+  for (const Up& u : ups) {
+    e = cudaMemcpyAsync(ws + u.off, u.src, u.n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl, s);
+  if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("counter reset: ") + cudaGetErrorString(e));
+
+  alignas(64) unsigned char tmap[128];
+  if (!encode_scratch_map_at(p, ws + p.off_scratch, tmap))
+    return fail(p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the no-allocation scratch ring");
+
+  LateralParams lp;
+  lp.frames = frames_dev;
+  lp.ring_start = 0;
+  lp.nx = p.nx; lp.ny = p.ny; lp.nl = p.nl;
+  lp.x0 = p.x0; lp.y0 = p.y0; lp.wx = p.wx; lp.wy = p.wy;
+  lp.wxp = p.wxp; lp.ntx = p.ntx;
+  lp.xtab = (const TapX*)(ws + p.off_xtab);
+  lp.ytab = (const Tap*)(ws + p.off_ytab);
+  lp.cx = (const float2*)(ws + p.off_cx);
+  lp.cy = (const float2*)(ws + p.off_cy);
+  lp.twx = (const float2*)(ws + p.off_twx);
+  lp.twy = (const float2*)(ws + p.off_twy);
+  lp.scratch = (float2*)(ws + p.off_scratch);
+  lp.inter = (float2*)(ws + p.off_inter);
+  lp.ctr = (Counters*)(ws + p.off_ctr);
+  lp.rows_done = (unsigned*)(ws + p.off_ctr + sizeof(Counters));
+  lp.cols_done = lp.rows_done + p.nl;
+  lp.sch = p.sch;
+  lp.stage_rows = p.stage_rows;
+  lp.stage_bytes = 0;
+  lp.xbuf_bytes = 0;
+  e = launch_lateral_with(p, lp, tmap, g_num_sms[dev], s);
+  if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("lateral kernel launch: ") + cudaGetErrorString(e));
+
+  AxialParams ap;
+  ap.inter = lp.inter;
+  ap.vol = vol_dev;
+  ap.cplx = (float2*)complex_dev;
+  ap.twl = (const float2*)(ws + p.off_twl);
+  ap.ox = (const float2*)(ws + p.off_ox);
+  ap.oy = (const float2*)(ws + p.off_oy);
+  ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
+  ap.power_scale = (float)(p.alpha * p.alpha);
+  ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
+  e = launch_axial(p, ap, s);
+  if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("axial kernel launch: ") + cudaGetErrorString(e));
+  return SSOCT_OK;
+}

@@ -195,4 +195,12 @@ size_t lateral_smem_bytes(const Plan& p);
 // Columns per column item of the lateral kernel for a column length ny.
 int lateral_col_band(int ny);
 
+// Used by the no-allocation entry point (noalloc.cu): the plan behind a handle,
+// a scratch-ring tensor map for scratch memory at an arbitrary device address,
+// and a lateral launch that takes the tensor map and SM count explicitly.
+Plan& plan_of(ssoct_plan h);
+bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out);
+cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap, int num_sms,
+                                cudaStream_t s);
+
 }  // namespace ssoct

@@ -150,6 +150,26 @@ bool encode_scratch_map(Plan& p) {
 
 }  // namespace
 
+namespace ssoct {
+
+Plan& plan_of(ssoct_plan h) { return h->p; }
+
+bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int band = lateral_col_band(p.ny);
+  cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.sch.slots * p.ny};
+  cuuint64_t strides[1] = {(cuuint64_t)2 * p.wxp * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)(p.ny < 256 ? p.ny : 256)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, scratch_dev, dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace ssoct
+
 extern "C" {
 
 const char* ssoct_status_string(ssoct_status s) {
