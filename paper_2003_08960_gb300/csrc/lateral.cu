@@ -99,6 +99,29 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// 1D bulk copy shared -> global (bulk async-group of the issuing thread).
+__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+// 2D tiled tensor copy shared -> global (box as set in the tensor map).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+               "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Order this thread's generic-proxy shared-memory writes before later async-proxy
+// (TMA) reads of them, and generic / async global accesses against each other.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // Barrier of the consumer warps only (named barrier 1); returns the OR of `v`.
 __device__ __forceinline__ bool consumers_sync_or(bool v) {
   unsigned r;
@@ -129,7 +152,7 @@ __host__ __device__ constexpr size_t row_stage_bytes(int nrows) {
 // jlo .. jlo + nrows - 1 (uint16) copied by the producer.
 template <int NX, int NY, bool FW>
 __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, const uint16_t* in,
-                                         unsigned char* xb, const float2* twx) {
+                                         unsigned char* xb, const float2* twx, float2* out) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
   constexpr int RPI = kThreads / N1;
   constexpr int LD = N1 + 1;  // padded exchange row: conflict-free transposed reads
@@ -199,29 +222,38 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = exr[k2 * LD + jj];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  // 4. window columns into the scratch slot of frame f (the producer checked it is free)
-  const unsigned long long pol_last = policy_evict_last();
-  float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
-  static_for<0, N2 / N1>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    const int k2 = j1 + N1 * i;
+  // 4. whole-frame plans: the row goes to the stage buffer (its inputs are dead)
+  //    and the producer writes the rows to the scratch slot with TMA; windowed
+  //    plans store their window columns directly
+  if constexpr (FW) {
+    float2* o = out + r * NX;
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const int k2 = j1 + N1 * i;
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      if constexpr (FW) {
-        st_cg_hint(dst + k2 + N2 * k1, a[i * N1 + k1], pol_last);
-      } else {
+      for (int k1 = 0; k1 < N1; ++k1) o[k2 + N2 * k1] = a[i * N1 + k1];
+    });
+    fence_proxy_async_smem();
+  } else {
+    const unsigned long long pol_last = policy_evict_last();
+    float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const int k2 = j1 + N1 * i;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
         const int kw = k2 + N2 * k1 - p.x0;
         if (kw >= 0 && kw < p.wx) st_cg_hint(dst + kw, a[i * N1 + k1], pol_last);
       }
-    }
-  });
+    });
+  }
 }
 
 // Column item: window columns [item*BC, item*BC + BC) of frame d.f; `tile` holds
 // the band [NY][BC] (complex) copied from the scratch slot by the producer.
 template <int NY, bool FW>
 __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, const float2* tile,
-                                         unsigned char* xb, const float2* twy) {
+                                         unsigned char* xb, const float2* twy, float2* out) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
   // padded k2 block: the 16 lanes of a half-warp read 16/BC k2 blocks at once,
@@ -247,24 +279,32 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[k2 * KP + jj * BC + b];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  const int kxw = d.item * BC + b;
-  if (kxw < p.wx) {
-    const unsigned long long pol_first = policy_evict_first();
-    float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)d.f * kTile + (kxw % kTile);
-    const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
+  if constexpr (FW) {
+    // [ky][BC] into the stage buffer (the band was consumed in pass A); the
+    // producer writes it into the intermediate with 2D tensor stores
     static_for<0, N2 / N1>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const int k2 = j1 + N1 * i;
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        if constexpr (FW) {
-          st_cg_hint(dst + (size_t)(k2 + N2 * k1) * row_pitch, a[i * N1 + k1], pol_first);
-        } else {
+      for (int k1 = 0; k1 < N1; ++k1) out[(k2 + N2 * k1) * BC + b] = a[i * N1 + k1];
+    });
+    fence_proxy_async_smem();
+  } else {
+    const int kxw = d.item * BC + b;
+    if (kxw < p.wx) {
+      const unsigned long long pol_first = policy_evict_first();
+      float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)d.f * kTile + (kxw % kTile);
+      const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
+      static_for<0, N2 / N1>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const int k2 = j1 + N1 * i;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
           const int kyw = k2 + N2 * k1 - p.y0;
           if (kyw >= 0 && kyw < p.wy) st_cg_hint(dst + (size_t)kyw * row_pitch, a[i * N1 + k1], pol_first);
         }
-      }
-    });
+      });
+    }
   }
 }
 
@@ -276,23 +316,46 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
 // mbarrier's acquire, so the consumers' stores are visible first).  Every wait
 // keeps publishing finished items, so a CTA never holds back a completion that
 // another CTA (or its own next item) is waiting for.
-template <int NX, int NY>
-__device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64_t* full_bar, uint64_t* done_bar,
-                         Desc* desc, unsigned char* stage0) {
+template <int NX, int NY, bool FW>
+__device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const CUtensorMap* tmap_inter,
+                         uint64_t* full_bar, uint64_t* done_bar, Desc* desc, unsigned char* stage0) {
   constexpr int RPI = kThreads / Split<NX>::N1;
   constexpr int BC = kThreads / Split<NY>::N1;
   constexpr int BOX_ROWS = NY < 256 ? NY : 256;
   const long long total = p.sch.total();
-  int busy_kind[2] = {-1, -1}, busy_f[2] = {0, 0};
+  int busy_kind[2] = {-1, -1}, busy_f[2] = {0, 0}, busy_item[2] = {0, 0};
   unsigned phase[2] = {0u, 0u};
+  // An item is finished when its consumers have arrived; for whole-frame plans
+  // the producer then writes the item's outputs from the stage buffer with TMA
+  // and waits for the writes before publishing the item.
+  auto finish = [&](int b) {
+    if constexpr (FW) {
+      const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
+      const int f = busy_f[b];
+      if (busy_kind[b] == kRowItem) {
+        float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + busy_item[b] * RPI) * p.wxp;
+#pragma unroll 1
+        for (int r = 0; r < RPI; ++r)
+          tma_store_1d(dst + (size_t)r * p.wxp, buf + (size_t)r * NX * sizeof(float2), (unsigned)(NX * sizeof(float2)));
+      } else {
+        const int b0 = busy_item[b] * BC;
+        const int x = 2 * (((b0 / kTile) * p.nl + f) * kTile + (b0 % kTile));
+#pragma unroll
+        for (int i = 0; i < NY / BOX_ROWS; ++i)
+          tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2));
+      }
+      bulk_commit();
+      bulk_wait_all();
+      fence_proxy_async_global();
+    }
+    red_release_gpu((busy_kind[b] == kRowItem ? p.rows_done : p.cols_done) + busy_f[b], 1u);
+    busy_kind[b] = -1;
+    phase[b] ^= 1u;
+  };
   auto service = [&]() {
 #pragma unroll
     for (int b = 0; b < 2; ++b)
-      if (busy_kind[b] >= 0 && mbar_test(&done_bar[b], phase[b])) {
-        red_release_gpu((busy_kind[b] == kRowItem ? p.rows_done : p.cols_done) + busy_f[b], 1u);
-        busy_kind[b] = -1;
-        phase[b] ^= 1u;
-      }
+      if (busy_kind[b] >= 0 && mbar_test(&done_bar[b], phase[b])) finish(b);
   };
   auto give_up = [&]() {
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
@@ -335,6 +398,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
         }
       }
     }
+    fence_proxy_async_global();  // the acquired data is read by TMA (async proxy)
     Desc d{kind, f, item, 0, 0};
     if (kind == kRowItem) {
       const Tap* yt = p.ytab + (size_t)f * NY;
@@ -383,6 +447,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
     }
     busy_kind[b] = kind;
     busy_f[b] = f;
+    busy_item[b] = item;
     // the next ticket, requested once this one is handed over (its round trip
     // overlaps the wait for the next free buffer)
     t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
@@ -400,7 +465,8 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
 
 template <int NX, int NY, bool FW>
 __global__ void __launch_bounds__(kCtaThreads, 1)
-    lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap) {
+    lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap,
+                   const __grid_constant__ CUtensorMap tmap_inter) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full_bar[2];
@@ -420,7 +486,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   float2* twx = reinterpret_cast<float2*>(xb + p.xbuf_bytes);
   float2* twy = twx + NX;
   if (tid >= kThreads) {
-    if (tid == kThreads) producer<NX, NY>(p, &tmap, full_bar, done_bar, desc, stage0);
+    if (tid == kThreads) producer<NX, NY, FW>(p, &tmap, &tmap_inter, full_bar, done_bar, desc, stage0);
     return;
   }
   for (int i = tid; i < NX; i += kThreads) twx[i] = ldg2(p.twx + i);
@@ -433,11 +499,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     if (consumers_sync_or(!ok)) break;
     const Desc d = desc[b];
     if (d.kind == kEndItem) break;
-    const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
+    unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     if (d.kind == kRowItem)
-      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb, twx);
+      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb, twx, reinterpret_cast<float2*>(buf));
     else
-      col_item<NY, FW>(p, d, reinterpret_cast<const float2*>(buf), xb, twy);
+      col_item<NY, FW>(p, d, reinterpret_cast<const float2*>(buf), xb, twy, reinterpret_cast<float2*>(buf));
     mbar_arrive(&done_bar[b]);
   }
 }
@@ -450,8 +516,11 @@ void smem_layout(const Plan& p, size_t& stage_bytes, size_t& xbuf_bytes, size_t&
   constexpr int N1y = Split<NY>::N1, N2y = Split<NY>::N2;
   constexpr int BCy = kThreads / N1y;
   const size_t in_rows = row_stage_bytes<NX>(p.stage_rows);
-  const size_t in_cols = (size_t)NY * BCy * sizeof(float2);
-  stage_bytes = ((in_rows > in_cols ? in_rows : in_cols) + 1023) / 1024 * 1024;
+  const size_t in_cols = (size_t)NY * BCy * sizeof(float2);             // also a column item's output
+  const size_t out_rows = (size_t)(kThreads / N1x) * NX * sizeof(float2);  // a row item's output (whole-frame plans)
+  size_t sbm = in_rows > in_cols ? in_rows : in_cols;
+  sbm = sbm > out_rows ? sbm : out_rows;
+  stage_bytes = (sbm + 1023) / 1024 * 1024;
   const size_t fl = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
   const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
   const size_t cols = (size_t)N2y * (N1y * BCy + (BCy < 16 ? BCy : 0)) * sizeof(float2);
@@ -469,36 +538,8 @@ size_t smem_for(const Plan& p) {
 }
 
 template <int NX, int NY, bool FW>
-cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, cudaStream_t s) {
-  size_t sb, xbb, smem;
-  smem_layout<NX, NY>(p, sb, xbb, smem);
-  LateralParams lp = lp_in;
-  lp.stage_bytes = (int)sb;
-  lp.xbuf_bytes = (int)xbb;
-  cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  const long long total = lp.sch.total();
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY, FW>, kCtaThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  int grid = (p.num_sms > 0 ? p.num_sms : 1) * per_sm;
-  if (grid > total) grid = (int)total;
-  lateral_kernel<NX, NY, FW><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(p.tmap));
-  return cudaGetLastError();
-}
-
-template <int NX, int NY>
-cudaError_t launch(const Plan& p, const LateralParams& lp, cudaStream_t s) {
-  const bool full = p.x0 == 0 && p.y0 == 0 && p.wx == NX && p.wy == NY;
-  return full ? launch_fw<NX, NY, true>(p, lp, s) : launch_fw<NX, NY, false>(p, lp, s);
-}
-
-// Same launch with the scratch-ring tensor map and the SM count given by the
-// caller (used when the scratch lives outside the plan's workspace).
-template <int NX, int NY, bool FW>
-cudaError_t launch_fw_with(const Plan& p, const LateralParams& lp_in, const void* tmap, int num_sms, cudaStream_t s) {
+cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, const void* tmap, const void* tmap_inter,
+                      int num_sms, cudaStream_t s) {
   size_t sb, xbb, smem;
   smem_layout<NX, NY>(p, sb, xbb, smem);
   LateralParams lp = lp_in;
@@ -514,15 +555,16 @@ cudaError_t launch_fw_with(const Plan& p, const LateralParams& lp_in, const void
   if (per_sm < 1) per_sm = 1;
   int grid = (num_sms > 0 ? num_sms : 1) * per_sm;
   if (grid > total) grid = (int)total;
-  lateral_kernel<NX, NY, FW><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(tmap));
+  lateral_kernel<NX, NY, FW><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(tmap),
+                                                             *reinterpret_cast<const CUtensorMap*>(tmap_inter));
   return cudaGetLastError();
 }
 
 template <int NX, int NY>
-cudaError_t launch_with(const Plan& p, const LateralParams& lp, const void* tmap, int num_sms, cudaStream_t s) {
-  const bool full = p.x0 == 0 && p.y0 == 0 && p.wx == NX && p.wy == NY;
-  return full ? launch_fw_with<NX, NY, true>(p, lp, tmap, num_sms, s)
-              : launch_fw_with<NX, NY, false>(p, lp, tmap, num_sms, s);
+cudaError_t launch(const Plan& p, const LateralParams& lp, const void* tmap, const void* tmap_inter, int num_sms,
+                   cudaStream_t s) {
+  return lateral_full_window(p) ? launch_fw<NX, NY, true>(p, lp, tmap, tmap_inter, num_sms, s)
+                                : launch_fw<NX, NY, false>(p, lp, tmap, tmap_inter, num_sms, s);
 }
 
 #define SSOCT_LATERAL_SIZES(X) \
@@ -546,19 +588,16 @@ size_t lateral_smem_bytes(const Plan& p) {
 
 int lateral_col_band(int ny) { return kThreads / split_n1(ny); }
 
-cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap, int num_sms,
-                                cudaStream_t s) {
-#define X(a, b) if (p.nx == a && p.ny == b) return launch_with<a, b>(p, lp, tmap, num_sms, s);
+cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap, const void* tmap_inter,
+                                int num_sms, cudaStream_t s) {
+#define X(a, b) if (p.nx == a && p.ny == b) return launch<a, b>(p, lp, tmap, tmap_inter, num_sms, s);
   SSOCT_LATERAL_SIZES(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s) {
-#define X(a, b) if (p.nx == a && p.ny == b) return launch<a, b>(p, lp, s);
-  SSOCT_LATERAL_SIZES(X)
-#undef X
-  return cudaErrorInvalidValue;
+  return launch_lateral_with(p, lp, p.tmap, p.tmap_inter, p.num_sms, s);
 }
 
 }  // namespace ssoct
