@@ -99,19 +99,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// 1D bulk copy shared -> global (bulk async-group of the issuing thread).
-__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, unsigned bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-               "r"(bytes)
+// 1D bulk copy shared -> global with an L2 policy (bulk async-group of the
+// issuing thread).
+__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, unsigned bytes, unsigned long long pol) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes), "l"(pol)
                : "memory");
 }
-// 2D tiled tensor copy shared -> global (box as set in the tensor map).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
-               "r"(y), "r"(smem_u32(src))
+// 2D tiled tensor copy shared -> global (box as set in the tensor map), L2 policy.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src,
+                                             unsigned long long pol) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
+                   map),
+               "r"(x), "r"(y), "r"(smem_u32(src)), "l"(pol)
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every committed group of this thread has finished reading shared memory
+__device__ __forceinline__ void bulk_wait_reads() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed group of this thread has finished writing global memory
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Order this thread's generic-proxy shared-memory writes before later async-proxy
 // (TMA) reads of them, and generic / async global accesses against each other.
@@ -325,9 +331,24 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
   const long long total = p.sch.total();
   int busy_kind[2] = {-1, -1}, busy_f[2] = {0, 0}, busy_item[2] = {0, 0};
   unsigned phase[2] = {0u, 0u};
-  // An item is finished when its consumers have arrived; for whole-frame plans
-  // the producer then writes the item's outputs from the stage buffer with TMA
-  // and waits for the writes before publishing the item.
+  // items whose outputs are written (TMA, whole-frame plans) but not yet published
+  int pend_n = 0, pend_kind[2] = {0, 0}, pend_f[2] = {0, 0};
+  const unsigned long long pol_last = policy_evict_last();
+  const unsigned long long pol_first = policy_evict_first();
+  auto publish = [&](int kind, int f) { red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u); };
+  // Publish written items once their TMA writes are complete.
+  auto flush = [&]() {
+    if (pend_n) {
+      bulk_wait_all();
+      fence_proxy_async_global();
+      for (int i = 0; i < pend_n; ++i) publish(pend_kind[i], pend_f[i]);
+      pend_n = 0;
+    }
+  };
+  // An item is finished when its consumers have arrived.  For whole-frame plans
+  // the producer then writes the item's outputs from the stage buffer with TMA;
+  // the buffer is free again once the copies have read it, and the item is
+  // published once the writes are complete (the next flush).
   auto finish = [&](int b) {
     if constexpr (FW) {
       const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
@@ -336,19 +357,24 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
         float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + busy_item[b] * RPI) * p.wxp;
 #pragma unroll 1
         for (int r = 0; r < RPI; ++r)
-          tma_store_1d(dst + (size_t)r * p.wxp, buf + (size_t)r * NX * sizeof(float2), (unsigned)(NX * sizeof(float2)));
+          tma_store_1d(dst + (size_t)r * p.wxp, buf + (size_t)r * NX * sizeof(float2), (unsigned)(NX * sizeof(float2)),
+                       pol_last);
       } else {
         const int b0 = busy_item[b] * BC;
         const int x = 2 * (((b0 / kTile) * p.nl + f) * kTile + (b0 % kTile));
 #pragma unroll
         for (int i = 0; i < NY / BOX_ROWS; ++i)
-          tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2));
+          tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
       }
       bulk_commit();
-      bulk_wait_all();
-      fence_proxy_async_global();
+      if (pend_n == 2) flush();
+      pend_kind[pend_n] = busy_kind[b];
+      pend_f[pend_n] = f;
+      ++pend_n;
+      bulk_wait_reads();
+    } else {
+      publish(busy_kind[b], busy_f[b]);
     }
-    red_release_gpu((busy_kind[b] == kRowItem ? p.rows_done : p.cols_done) + busy_f[b], 1u);
     busy_kind[b] = -1;
     phase[b] ^= 1u;
   };
@@ -389,6 +415,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
         const unsigned long long t0 = global_timer_ns();
         while (ld_acquire_gpu(dep) < target) {
           service();
+          flush();
           if (*(volatile unsigned*)&p.ctr->abort || global_timer_ns() - t0 > kProducerWaitNs) {
             give_up();
             kind = kEndItem;
@@ -410,6 +437,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       const unsigned long long t0 = global_timer_ns();
       while (busy_kind[b] >= 0) {
         service();
+        if (busy_kind[b] >= 0) flush();
         if (busy_kind[b] >= 0 && global_timer_ns() - t0 > kProducerWaitNs) {
           give_up();
           kind = kEndItem;  // the buffer's old item is lost; consumers still get an end mark
@@ -451,6 +479,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
     // the next ticket, requested once this one is handed over (its round trip
     // overlaps the wait for the next free buffer)
     t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
+    flush();
   }
   // drain: publish what is still in flight
   const unsigned long long t0 = global_timer_ns();
@@ -461,6 +490,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       break;
     }
   }
+  flush();
 }
 
 template <int NX, int NY, bool FW>
