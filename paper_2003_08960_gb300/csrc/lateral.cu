@@ -99,13 +99,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// 1D bulk copy shared -> global with an L2 policy (bulk async-group of the
-// issuing thread).
-__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, unsigned bytes, unsigned long long pol) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
-               "r"(smem_u32(src)), "r"(bytes), "l"(pol)
-               : "memory");
-}
 // 2D tiled tensor copy shared -> global (box as set in the tensor map), L2 policy.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src,
                                              unsigned long long pol) {
@@ -158,7 +151,7 @@ __host__ __device__ constexpr size_t row_stage_bytes(int nrows) {
 // jlo .. jlo + nrows - 1 (uint16) copied by the producer.
 template <int NX, int NY, bool FW>
 __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, const uint16_t* in,
-                                         unsigned char* xb, const float2* twx, float2* out) {
+                                         unsigned char* xb, const float2* twx) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
   constexpr int RPI = kThreads / N1;
   constexpr int LD = N1 + 1;  // padded exchange row: conflict-free transposed reads
@@ -228,31 +221,23 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = exr[k2 * LD + jj];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  // 4. whole-frame plans: the row goes to the stage buffer (its inputs are dead)
-  //    and the producer writes the rows to the scratch slot with TMA; windowed
-  //    plans store their window columns directly
-  if constexpr (FW) {
-    float2* o = out + r * NX;
-    static_for<0, N2 / N1>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const int k2 = j1 + N1 * i;
+  // 4. the window columns into the scratch slot of frame f (the producer checked
+  //    it is free): contiguous 256-byte runs per warp, kept in L2
+  const unsigned long long pol_last = policy_evict_last();
+  float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) o[k2 + N2 * k1] = a[i * N1 + k1];
-    });
-    fence_proxy_async_smem();
-  } else {
-    const unsigned long long pol_last = policy_evict_last();
-    float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
-    static_for<0, N2 / N1>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const int k2 = j1 + N1 * i;
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
+    for (int k1 = 0; k1 < N1; ++k1) {
+      if constexpr (FW) {
+        st_cg_hint(dst + k2 + N2 * k1, a[i * N1 + k1], pol_last);
+      } else {
         const int kw = k2 + N2 * k1 - p.x0;
         if (kw >= 0 && kw < p.wx) st_cg_hint(dst + kw, a[i * N1 + k1], pol_last);
       }
-    });
-  }
+    }
+  });
 }
 
 // Column item: window columns [item*BC, item*BC + BC) of frame d.f; `tile` holds
@@ -333,7 +318,6 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
   unsigned phase[2] = {0u, 0u};
   // items whose outputs are written (TMA, whole-frame plans) but not yet published
   int pend_n = 0, pend_kind[2] = {0, 0}, pend_f[2] = {0, 0};
-  const unsigned long long pol_last = policy_evict_last();
   const unsigned long long pol_first = policy_evict_first();
   auto publish = [&](int kind, int f) { red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u); };
   // Publish written items once their TMA writes are complete.
@@ -345,31 +329,24 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       pend_n = 0;
     }
   };
-  // An item is finished when its consumers have arrived.  For whole-frame plans
-  // the producer then writes the item's outputs from the stage buffer with TMA;
-  // the buffer is free again once the copies have read it, and the item is
-  // published once the writes are complete (the next flush).
+  // An item is finished when its consumers have arrived (their stores are then
+  // ordered before the publishing release).  A column item of a whole-frame plan
+  // left its output band in the stage buffer: the producer writes it into the
+  // intermediate with 2D tensor stores; the buffer is free again once the copies
+  // have read it, and the item is published once the writes are complete (the
+  // next flush).
   auto finish = [&](int b) {
-    if constexpr (FW) {
+    if (FW && busy_kind[b] == kColItem) {
       const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
-      const int f = busy_f[b];
-      if (busy_kind[b] == kRowItem) {
-        float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + busy_item[b] * RPI) * p.wxp;
-#pragma unroll 1
-        for (int r = 0; r < RPI; ++r)
-          tma_store_1d(dst + (size_t)r * p.wxp, buf + (size_t)r * NX * sizeof(float2), (unsigned)(NX * sizeof(float2)),
-                       pol_last);
-      } else {
-        const int b0 = busy_item[b] * BC;
-        const int x = 2 * (((b0 / kTile) * p.nl + f) * kTile + (b0 % kTile));
+      const int b0 = busy_item[b] * BC;
+      const int x = 2 * (((b0 / kTile) * p.nl + busy_f[b]) * kTile + (b0 % kTile));
 #pragma unroll
-        for (int i = 0; i < NY / BOX_ROWS; ++i)
-          tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
-      }
+      for (int i = 0; i < NY / BOX_ROWS; ++i)
+        tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
       bulk_commit();
       if (pend_n == 2) flush();
       pend_kind[pend_n] = busy_kind[b];
-      pend_f[pend_n] = f;
+      pend_f[pend_n] = busy_f[b];
       ++pend_n;
       bulk_wait_reads();
     } else {
@@ -531,7 +508,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     if (d.kind == kEndItem) break;
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     if (d.kind == kRowItem)
-      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb, twx, reinterpret_cast<float2*>(buf));
+      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb, twx);
     else
       col_item<NY, FW>(p, d, reinterpret_cast<const float2*>(buf), xb, twy, reinterpret_cast<float2*>(buf));
     mbar_arrive(&done_bar[b]);
@@ -546,10 +523,8 @@ void smem_layout(const Plan& p, size_t& stage_bytes, size_t& xbuf_bytes, size_t&
   constexpr int N1y = Split<NY>::N1, N2y = Split<NY>::N2;
   constexpr int BCy = kThreads / N1y;
   const size_t in_rows = row_stage_bytes<NX>(p.stage_rows);
-  const size_t in_cols = (size_t)NY * BCy * sizeof(float2);             // also a column item's output
-  const size_t out_rows = (size_t)(kThreads / N1x) * NX * sizeof(float2);  // a row item's output (whole-frame plans)
-  size_t sbm = in_rows > in_cols ? in_rows : in_cols;
-  sbm = sbm > out_rows ? sbm : out_rows;
+  const size_t in_cols = (size_t)NY * BCy * sizeof(float2);  // also a column item's output
+  const size_t sbm = in_rows > in_cols ? in_rows : in_cols;
   stage_bytes = (sbm + 1023) / 1024 * 1024;
   const size_t fl = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
   const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
