@@ -4,11 +4,13 @@
 // Each CTA has one producer warp and eight consumer warps.  The producer takes
 // work items from a device ticket counter (in the order LateralSchedule
 // defines), waits until an item's inputs are ready, and copies them into one of
-// two shared-memory stage buffers with the Tensor Memory Accelerator (a 1D bulk
-// copy of the uint16 input rows, or 2D tensor copies of an L2 scratch column
-// band), handing the item over through an mbarrier.  Consumers only compute; when
-// they are done with an item they arrive on a second mbarrier, and the producer
-// then publishes the item's completion to the other CTAs.  Items:
+// three shared-memory stage buffers with the Tensor Memory Accelerator (1D bulk
+// copies of the uint16 input rows and tap tables, or 2D tensor copies of an L2
+// scratch column band), handing the item over through an mbarrier.  Consumers
+// only compute, in place in the stage buffer; when they are done they arrive on
+// a second mbarrier, and the producer writes the item's outputs with TMA stores
+// (whole-frame plans) and publishes the item's completion to the other CTAs.
+// Items:
 //  * row item (frame f, band of rows): stage the input rows the band needs in
 //    shared memory as float, resample them with the frame's separable linear-
 //    interpolation taps, multiply by the input chirp (centring phase folded in),
@@ -99,6 +101,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// 1D bulk copy shared -> global with an L2 policy (bulk async-group of the
+// issuing thread).
+__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, unsigned bytes, unsigned long long pol) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes), "l"(pol)
+               : "memory");
+}
 // 2D tiled tensor copy shared -> global (box as set in the tensor map), L2 policy.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src,
                                              unsigned long long pol) {
@@ -134,150 +143,150 @@ __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;
 
 // ---------------------------------------------------------------- consumer work
 
+constexpr int kStages = 3;  // stage buffers: one computed, one loaded ahead, one draining its stores
+
 // A row item's stage buffer: nrows uint16 input rows, then (16-byte aligned) the
-// frame's NX x taps (TapX, 16 bytes each), the RPI y taps of its rows (Tap) and
-// the RPI y chirps of its rows (float2).
+// frame's NX x taps, the RPI y taps and the RPI y chirps of its rows.
 template <int NX>
-__host__ __device__ constexpr int taps_offset_elems(int nrows) {
-  return (nrows * NX + 7) / 8 * 8;  // in uint16 elements; NX >= 64 keeps it 16-byte aligned
+__host__ __device__ constexpr size_t row_taps_offset(int nrows) {
+  return ((size_t)nrows * NX * sizeof(uint16_t) + 15) / 16 * 16;
 }
 template <int NX>
 __host__ __device__ constexpr size_t row_stage_bytes(int nrows) {
-  return (size_t)taps_offset_elems<NX>(nrows) * 2 + (size_t)NX * sizeof(TapX) +
+  return row_taps_offset<NX>(nrows) + (size_t)NX * sizeof(Tap) +
          (size_t)(kThreads / split_n1(NX)) * (sizeof(Tap) + sizeof(float2));
 }
 
-// Row item: rows [item*RPI, item*RPI + RPI) of frame d.f; `in` holds input rows
-// jlo .. jlo + nrows - 1 (uint16) copied by the producer.
+// Position of element (k2, j1) in a row's N2 x N1 transpose block: the column is
+// XOR-swizzled by k2 so that both the writes (fixed k2, all j1) and the
+// transposed reads (fixed j1, all k2) hit distinct banks without padding.
+template <int N1>
+__device__ __forceinline__ int xswz(int k2, int j1) {
+  return k2 * N1 + (j1 ^ (k2 & (N1 - 1)));
+}
+
+__device__ __forceinline__ float u16_to_f(unsigned short u) {
+  return __int_as_float(0x4B000000 | (unsigned)u) - 8388608.0f;  // 2^23 + u, exact
+}
+
+// Row item: rows [item*RPI, item*RPI + RPI) of frame d.f.  The stage buffer holds
+// input rows jlo .. jlo + nrows - 1 (uint16) and the taps; it then serves as the
+// transpose block and, for whole-frame plans, as the output [RPI][NX].
 template <int NX, int NY, bool FW>
-__device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, const uint16_t* in,
-                                         unsigned char* xb, const float2* twx) {
+__device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, unsigned char* buf,
+                                         const float2* twx, const float2* cxs) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
   constexpr int RPI = kThreads / N1;
-  constexpr int LD = N1 + 1;  // padded exchange row: conflict-free transposed reads
-  constexpr int SP = NX + 2 * kStagePad;
   const int tid = threadIdx.x;
   const int r = tid / N1;
   const int j1 = tid % N1;
   const int f = d.f;
   const int y = d.item * RPI + r;
-  // 1. uint16 rows -> float rows padded with zeros on both sides, so that taps
-  //    outside the frame read 0
-  float* stage = reinterpret_cast<float*>(xb);
-  {
-    const uint4* s4 = reinterpret_cast<const uint4*>(in);
-    const int nvec = d.nrows * (NX / 8);
-    for (int i = tid; i < nvec; i += kThreads) {
-      const uint4 v = s4[i];
-      float4* d4 = reinterpret_cast<float4*>(stage + (i / (NX / 8)) * SP + kStagePad + (i % (NX / 8)) * 8);
-      d4[0] = make_float4(u16lo_to_f(v.x), u16hi_to_f(v.x), u16lo_to_f(v.y), u16hi_to_f(v.y));
-      d4[1] = make_float4(u16lo_to_f(v.z), u16hi_to_f(v.z), u16lo_to_f(v.w), u16hi_to_f(v.w));
-    }
-    for (int i = tid; i < d.nrows; i += kThreads) {
-      stage[i * SP + kStagePad - 1] = 0.f;
-      stage[i * SP + kStagePad + NX] = 0.f;
-    }
-  }
-  consumers_sync();
-  // 2. Eq. 5 resample x input chirp, elements n = j1 + N1 * j2 of row y
-  const TapX* xtaps = reinterpret_cast<const TapX*>(in + taps_offset_elems<NX>(d.nrows));
-  const Tap* ytaps = reinterpret_cast<const Tap*>(xtaps + NX);
+  const uint16_t* in = reinterpret_cast<const uint16_t*>(buf);
+  const Tap* xtaps = reinterpret_cast<const Tap*>(buf + row_taps_offset<NX>(d.nrows));
+  const Tap* ytaps = xtaps + NX;
   const float2* ychirp = reinterpret_cast<const float2*>(ytaps + RPI);
+  // 1. Eq. 5 resample (taps outside the frame carry weight 0) x input chirp,
+  //    elements n = j1 + N1 * j2 of row y
   float2 a[N2];
   {
     const Tap ty = ytaps[r];
-    const float* r0 = stage + (ty.base - d.jlo) * SP + kStagePad;
-    const float* r1 = r0 + SP;
-    const float4* xt = reinterpret_cast<const float4*>(xtaps);
+    const uint16_t* r0 = in + (ty.base - d.jlo) * NX;
+    const uint16_t* r1 = r0 + NX;
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) {
       const int n = j1 + N1 * j2;
-      const float4 t = xt[n];
-      const int bx = __float_as_int(t.x);
-      const float a0 = r0[bx], a1 = r0[bx + 1], b0 = r1[bx], b1 = r1[bx + 1];
-      const float v0 = fmaf(t.y, a1 - a0, a0);
-      const float v1 = fmaf(t.y, b1 - b0, b0);
+      const Tap t = xtaps[n];
+      const float v0 = fmaf(t.w0, u16_to_f(r0[t.base]), t.w1 * u16_to_f(r0[t.base + 1]));
+      const float v1 = fmaf(t.w0, u16_to_f(r1[t.base]), t.w1 * u16_to_f(r1[t.base + 1]));
       const float v = fmaf(ty.w0, v0, ty.w1 * v1);
-      a[j2] = make_float2(v * t.z, v * t.w);
+      const float2 c = cxs[n];
+      a[j2] = make_float2(v * c.x, v * c.y);
     }
   }
-  // 3. row DFT (+ sign of Eq. 6): N2-point DFT in registers, twiddle with the
-  //    row's y chirp folded in, transpose through shared memory, N1-point DFTs
+  // 2. row DFT (+ sign of Eq. 6): N2-point DFT in registers, twiddle with the
+  //    row's y chirp folded in, transpose in the stage buffer, N1-point DFTs
   Dft<N2, 1>::template run<1, 0>(a);
   {
     const float2 cyv = ychirp[r];
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
   }
-  consumers_sync();  // the float rows are dead: the exchange reuses them
-  float2* exr = reinterpret_cast<float2*>(xb) + r * (N2 * LD);
+  consumers_sync();  // every input of the buffer has been read
+  float2* ex = reinterpret_cast<float2*>(buf) + r * NX;  // this row's block (N2 x N1 = NX values)
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) exr[k2 * LD + j1] = a[k2];
+  for (int k2 = 0; k2 < N2; ++k2) ex[xswz<N1>(k2, j1)] = a[k2];
   __syncwarp();  // a row's N1 threads lie in one warp
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
 #pragma unroll
-    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = exr[k2 * LD + jj];
+    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[xswz<N1>(k2, jj)];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  // 4. the window columns into the scratch slot of frame f (the producer checked
-  //    it is free): contiguous 256-byte runs per warp, kept in L2
-  const unsigned long long pol_last = policy_evict_last();
-  float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
-  static_for<0, N2 / N1>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    const int k2 = j1 + N1 * i;
+  if constexpr (FW) {
+    // 3. the row in natural order over its own block; the producer writes the
+    //    RPI rows to the scratch slot with TMA
+    __syncwarp();
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const int k2 = j1 + N1 * i;
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      if constexpr (FW) {
-        st_cg_hint(dst + k2 + N2 * k1, a[i * N1 + k1], pol_last);
-      } else {
+      for (int k1 = 0; k1 < N1; ++k1) ex[k2 + N2 * k1] = a[i * N1 + k1];
+    });
+    fence_proxy_async_smem();
+  } else {
+    // 3. window columns straight into the scratch slot of frame f
+    const unsigned long long pol_last = policy_evict_last();
+    float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const int k2 = j1 + N1 * i;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
         const int kw = k2 + N2 * k1 - p.x0;
         if (kw >= 0 && kw < p.wx) st_cg_hint(dst + kw, a[i * N1 + k1], pol_last);
       }
-    }
-  });
+    });
+  }
 }
 
-// Column item: window columns [item*BC, item*BC + BC) of frame d.f; `tile` holds
-// the band [NY][BC] (complex) copied from the scratch slot by the producer.
+// Column item: window columns [item*BC, item*BC + BC) of frame d.f.  The stage
+// buffer holds the band [NY][BC] copied from the scratch slot; both DFT passes
+// work in place, and whole-frame plans leave the output [NY][BC] there for the
+// producer's tensor store.
 template <int NY, bool FW>
-__device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, const float2* tile,
-                                         unsigned char* xb, const float2* twy, float2* out) {
+__device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, unsigned char* buf,
+                                         const float2* twy) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
-  // padded k2 block: the 16 lanes of a half-warp read 16/BC k2 blocks at once,
-  // shifted by 2*BC banks each, so they never share a bank
-  constexpr int KP = N1 * BC + (BC < 16 ? BC : 0);
   const int tid = threadIdx.x;
   const int b = tid % BC;
   const int j1 = tid / BC;
+  float2* tile = reinterpret_cast<float2*>(buf);
   float2 a[N2];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = tile[(j1 + N1 * j2) * BC + b];
   Dft<N2, 1>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], twy[k2 * N1 + j1]);
-  float2* ex = reinterpret_cast<float2*>(xb);
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) ex[k2 * KP + j1 * BC + b] = a[k2];
+  for (int k2 = 0; k2 < N2; ++k2) tile[(j1 + N1 * k2) * BC + b] = a[k2];  // the rows this thread read
   consumers_sync();
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
 #pragma unroll
-    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[k2 * KP + jj * BC + b];
+    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = tile[(jj + N1 * k2) * BC + b];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
   if constexpr (FW) {
-    // [ky][BC] into the stage buffer (the band was consumed in pass A); the
-    // producer writes it into the intermediate with 2D tensor stores
+    consumers_sync();  // every transposed read is done
     static_for<0, N2 / N1>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const int k2 = j1 + N1 * i;
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) out[(k2 + N2 * k1) * BC + b] = a[i * N1 + k1];
+      for (int k1 = 0; k1 < N1; ++k1) tile[(k2 + N2 * k1) * BC + b] = a[i * N1 + k1];
     });
     fence_proxy_async_smem();
   } else {
@@ -301,12 +310,13 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
 
 // ---------------------------------------------------------------- producer
 
-// Producer warp, one thread.  Buffer b holds at most one item; an item is
-// "busy" from its hand-over until the consumers arrive on done[b], at which
-// point its completion is published to other CTAs (red.release after the
-// mbarrier's acquire, so the consumers' stores are visible first).  Every wait
-// keeps publishing finished items, so a CTA never holds back a completion that
-// another CTA (or its own next item) is waiting for.
+// Producer warp, one thread.  Stage buffer b holds at most one item from its
+// hand-over until (a) the consumers arrive on done[b] and, for whole-frame plans,
+// (b) the TMA stores of the item's outputs have read the buffer.  An item is
+// published to other CTAs (red.release on its frame's counter) once its outputs
+// are in global memory: right after done[b] when the consumers stored them,
+// after the TMA writes complete otherwise.  Every wait keeps servicing finished
+// items, so a CTA never holds back a completion another CTA is waiting for.
 template <int NX, int NY, bool FW>
 __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const CUtensorMap* tmap_inter,
                          uint64_t* full_bar, uint64_t* done_bar, Desc* desc, unsigned char* stage0) {
@@ -314,13 +324,21 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
   constexpr int BC = kThreads / Split<NY>::N1;
   constexpr int BOX_ROWS = NY < 256 ? NY : 256;
   const long long total = p.sch.total();
-  int busy_kind[2] = {-1, -1}, busy_f[2] = {0, 0}, busy_item[2] = {0, 0};
-  unsigned phase[2] = {0u, 0u};
-  // items whose outputs are written (TMA, whole-frame plans) but not yet published
-  int pend_n = 0, pend_kind[2] = {0, 0}, pend_f[2] = {0, 0};
+  int st_kind[kStages], st_f[kStages], st_item[kStages];
+  bool st_storing[kStages];
+  unsigned phase[kStages];
+#pragma unroll
+  for (int b = 0; b < kStages; ++b) {
+    st_kind[b] = -1;
+    st_f[b] = st_item[b] = 0;
+    st_storing[b] = false;
+    phase[b] = 0u;
+  }
+  int pend_n = 0, pend_kind[kStages], pend_f[kStages];
+  const unsigned long long pol_last = policy_evict_last();
   const unsigned long long pol_first = policy_evict_first();
   auto publish = [&](int kind, int f) { red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u); };
-  // Publish written items once their TMA writes are complete.
+  // publish items whose TMA writes are complete
   auto flush = [&]() {
     if (pend_n) {
       bulk_wait_all();
@@ -329,49 +347,64 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       pend_n = 0;
     }
   };
-  // An item is finished when its consumers have arrived (their stores are then
-  // ordered before the publishing release).  A column item of a whole-frame plan
-  // left its output band in the stage buffer: the producer writes it into the
-  // intermediate with 2D tensor stores; the buffer is free again once the copies
-  // have read it, and the item is published once the writes are complete (the
-  // next flush).
-  auto finish = [&](int b) {
-    if (FW && busy_kind[b] == kColItem) {
-      const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
-      const int b0 = busy_item[b] * BC;
-      const int x = 2 * (((b0 / kTile) * p.nl + busy_f[b]) * kTile + (b0 % kTile));
+  // free the buffers whose TMA stores have read them
+  auto release_reads = [&]() {
+    bool any = false;
 #pragma unroll
-      for (int i = 0; i < NY / BOX_ROWS; ++i)
-        tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
-      bulk_commit();
-      if (pend_n == 2) flush();
-      pend_kind[pend_n] = busy_kind[b];
-      pend_f[pend_n] = busy_f[b];
-      ++pend_n;
-      bulk_wait_reads();
-    } else {
-      publish(busy_kind[b], busy_f[b]);
-    }
-    busy_kind[b] = -1;
+    for (int b = 0; b < kStages; ++b) any |= st_storing[b];
+    if (!any) return;
+    bulk_wait_reads();
+#pragma unroll
+    for (int b = 0; b < kStages; ++b)
+      if (st_storing[b]) {
+        st_storing[b] = false;
+        st_kind[b] = -1;
+      }
+  };
+  auto finish = [&](int b) {
     phase[b] ^= 1u;
+    if constexpr (FW) {
+      const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
+      if (st_kind[b] == kRowItem) {
+        float2* dst = p.scratch + ((size_t)(st_f[b] % p.sch.slots) * NY + st_item[b] * RPI) * p.wxp;
+#pragma unroll 1
+        for (int r = 0; r < RPI; ++r)
+          tma_store_1d(dst + (size_t)r * p.wxp, buf + (size_t)r * NX * sizeof(float2), (unsigned)(NX * sizeof(float2)),
+                       pol_last);
+      } else {
+        const int b0 = st_item[b] * BC;
+        const int x = 2 * (((b0 / kTile) * p.nl + st_f[b]) * kTile + (b0 % kTile));
+#pragma unroll
+        for (int i = 0; i < NY / BOX_ROWS; ++i)
+          tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
+      }
+      bulk_commit();
+      if (pend_n == kStages) flush();
+      pend_kind[pend_n] = st_kind[b];
+      pend_f[pend_n] = st_f[b];
+      ++pend_n;
+      st_storing[b] = true;
+    } else {
+      publish(st_kind[b], st_f[b]);
+      st_kind[b] = -1;
+    }
   };
   auto service = [&]() {
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
-      if (busy_kind[b] >= 0 && mbar_test(&done_bar[b], phase[b])) finish(b);
+    for (int b = 0; b < kStages; ++b)
+      if (st_kind[b] >= 0 && !st_storing[b] && mbar_test(&done_bar[b], phase[b])) finish(b);
   };
   auto give_up = [&]() {
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
     atomicExch(&p.ctr->abort, 1u);
   };
-  // The producer prepares item s (ticket, dependency, descriptor) while the
-  // consumers still hold both buffers, and only the copy issue waits for buffer
-  // s & 1 to come free.  A CTA holds at most one unstarted, unpublished ticket;
-  // the lowest unfinished ticket is always one its CTA is working on or has
-  // handed over, so the queue drains.
+  // The producer prepares item s (ticket, dependency, descriptor) before its
+  // buffer is free, and only the copy issue waits for the buffer.  A CTA holds
+  // at most one unstarted, unpublished ticket; the lowest unfinished ticket is
+  // always one its CTA is working on or has handed over, so the queue drains.
   unsigned t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-  for (int s = 0;; ++s) {
-    const int b = s & 1;
+  int b = 0;
+  for (;; b = (b + 1 == kStages) ? 0 : b + 1) {
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     const unsigned t = t_next;
     int kind = kEndItem, f = 0, item = 0;
@@ -392,6 +425,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
         const unsigned long long t0 = global_timer_ns();
         while (ld_acquire_gpu(dep) < target) {
           service();
+          release_reads();
           flush();
           if (*(volatile unsigned*)&p.ctr->abort || global_timer_ns() - t0 > kProducerWaitNs) {
             give_up();
@@ -409,13 +443,15 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       d.jlo = yt[item * RPI].base;
       d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
     }
-    // 2. the buffer's previous item must be finished
-    if (busy_kind[b] >= 0) {
+    // 2. the buffer's previous item must be finished (and its stores must have
+    //    read it)
+    if (st_kind[b] >= 0) {
       const unsigned long long t0 = global_timer_ns();
-      while (busy_kind[b] >= 0) {
+      while (st_kind[b] >= 0) {
         service();
-        if (busy_kind[b] >= 0) flush();
-        if (busy_kind[b] >= 0 && global_timer_ns() - t0 > kProducerWaitNs) {
+        if (st_kind[b] >= 0 && st_storing[b]) release_reads();
+        if (st_kind[b] >= 0) flush();
+        if (st_kind[b] >= 0 && global_timer_ns() - t0 > kProducerWaitNs) {
           give_up();
           kind = kEndItem;  // the buffer's old item is lost; consumers still get an end mark
           break;
@@ -428,13 +464,13 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       mbar_arrive(&full_bar[b]);
       break;
     }
+    desc[b] = d;
     if (kind == kRowItem) {
       const unsigned bytes = (unsigned)(d.nrows * NX * sizeof(uint16_t));
-      const unsigned tap_off = (unsigned)(taps_offset_elems<NX>(d.nrows) * sizeof(uint16_t));
-      const unsigned tap_bytes = (unsigned)(NX * sizeof(TapX));
+      const unsigned tap_off = (unsigned)row_taps_offset<NX>(d.nrows);
+      const unsigned tap_bytes = (unsigned)(NX * sizeof(Tap));
       const unsigned yt_bytes = (unsigned)(RPI * sizeof(Tap));
       const unsigned cy_bytes = (unsigned)(RPI * sizeof(float2));
-      desc[b] = d;
       mbar_arrive_tx(&full_bar[b], bytes + tap_bytes + yt_bytes + cy_bytes);
       const int fr = (p.ring_start + f) % p.nl;
       tma_load_1d(buf, p.frames + ((size_t)fr * NY + d.jlo) * NX, bytes, &full_bar[b]);
@@ -442,7 +478,6 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       tma_load_1d(buf + tap_off + tap_bytes, p.ytab + (size_t)f * NY + item * RPI, yt_bytes, &full_bar[b]);
       tma_load_1d(buf + tap_off + tap_bytes + yt_bytes, p.cy + item * RPI, cy_bytes, &full_bar[b]);
     } else {
-      desc[b] = d;
       mbar_arrive_tx(&full_bar[b], (unsigned)(NY * BC * sizeof(float2)));
       const int x = 2 * item * BC;
       const int y0 = (f % p.sch.slots) * NY;
@@ -450,19 +485,23 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       for (int i = 0; i < NY / BOX_ROWS; ++i)
         tma_load_2d(buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), tmap, x, y0 + i * BOX_ROWS, &full_bar[b]);
     }
-    busy_kind[b] = kind;
-    busy_f[b] = f;
-    busy_item[b] = item;
+    st_kind[b] = kind;
+    st_f[b] = f;
+    st_item[b] = item;
     // the next ticket, requested once this one is handed over (its round trip
     // overlaps the wait for the next free buffer)
     t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-    flush();
   }
   // drain: publish what is still in flight
   const unsigned long long t0 = global_timer_ns();
-  while (busy_kind[0] >= 0 || busy_kind[1] >= 0) {
+  for (;;) {
     service();
-    if ((busy_kind[0] >= 0 || busy_kind[1] >= 0) && global_timer_ns() - t0 > kProducerWaitNs) {
+    release_reads();
+    bool busy = false;
+#pragma unroll
+    for (int i = 0; i < kStages; ++i) busy |= st_kind[i] >= 0;
+    if (!busy) break;
+    if (global_timer_ns() - t0 > kProducerWaitNs) {
       give_up();
       break;
     }
@@ -476,80 +515,84 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
                    const __grid_constant__ CUtensorMap tmap_inter) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full_bar[2];
-  __shared__ __align__(8) uint64_t done_bar[2];
-  __shared__ Desc desc[2];
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t done_bar[kStages];
+  __shared__ Desc desc[kStages];
   const int tid = threadIdx.x;
   if (tid == 0) {
-    mbar_init(&full_bar[0], 1);
-    mbar_init(&full_bar[1], 1);
-    mbar_init(&done_bar[0], kThreads);
-    mbar_init(&done_bar[1], kThreads);
+#pragma unroll
+    for (int b = 0; b < kStages; ++b) {
+      mbar_init(&full_bar[b], 1);
+      mbar_init(&done_bar[b], kThreads);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   unsigned char* stage0 = smem;
-  unsigned char* xb = smem + 2 * (size_t)p.stage_bytes;
-  float2* twx = reinterpret_cast<float2*>(xb + p.xbuf_bytes);
+  float2* twx = reinterpret_cast<float2*>(smem + kStages * (size_t)p.stage_bytes);
   float2* twy = twx + NX;
+  float2* cxs = twy + NY;
   if (tid >= kThreads) {
     if (tid == kThreads) producer<NX, NY, FW>(p, &tmap, &tmap_inter, full_bar, done_bar, desc, stage0);
     return;
   }
-  for (int i = tid; i < NX; i += kThreads) twx[i] = ldg2(p.twx + i);
+  for (int i = tid; i < NX; i += kThreads) {
+    twx[i] = ldg2(p.twx + i);
+    cxs[i] = ldg2(p.cx + i);
+  }
   for (int i = tid; i < NY; i += kThreads) twy[i] = ldg2(p.twy + i);
   // (visible to all consumers after the first consumers_sync_or below)
-  for (int s = 0;; ++s) {
-    const int b = s & 1;
-    const bool ok = mbar_wait(&full_bar[b], (unsigned)((s >> 1) & 1), p.ctr, kConsumerWaitNs);
-    // all consumers agree, and the previous item's readers of xb are done
+  int b = 0;
+  unsigned use = 0;  // completions of full[b] seen so far, per pass over the buffers
+  for (;;) {
+    const bool ok = mbar_wait(&full_bar[b], use & 1u, p.ctr, kConsumerWaitNs);
+    // all consumers agree, and the previous item is finished everywhere
     if (consumers_sync_or(!ok)) break;
     const Desc d = desc[b];
     if (d.kind == kEndItem) break;
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     if (d.kind == kRowItem)
-      row_item<NX, NY, FW>(p, d, reinterpret_cast<const uint16_t*>(buf), xb, twx);
+      row_item<NX, NY, FW>(p, d, buf, twx, cxs);
     else
-      col_item<NY, FW>(p, d, reinterpret_cast<const float2*>(buf), xb, twy, reinterpret_cast<float2*>(buf));
+      col_item<NY, FW>(p, d, buf, twy);
     mbar_arrive(&done_bar[b]);
+    if (++b == kStages) {
+      b = 0;
+      ++use;
+    }
   }
 }
 
-// Shared memory: two stage buffers (input rows of a row item, or a column band)
-// and one exchange buffer (float rows / row transpose / column transpose).
+// Shared memory: three stage buffers (a row item's inputs / transpose / output,
+// or a column band), then the row and column twiddles and the x input chirp.
 template <int NX, int NY>
-void smem_layout(const Plan& p, size_t& stage_bytes, size_t& xbuf_bytes, size_t& total) {
-  constexpr int N1x = Split<NX>::N1, N2x = Split<NX>::N2;
-  constexpr int N1y = Split<NY>::N1, N2y = Split<NY>::N2;
+void smem_layout(const Plan& p, size_t& stage_bytes, size_t& total) {
+  constexpr int N1y = Split<NY>::N1;
   constexpr int BCy = kThreads / N1y;
+  constexpr int RPI = kThreads / Split<NX>::N1;
   const size_t in_rows = row_stage_bytes<NX>(p.stage_rows);
-  const size_t in_cols = (size_t)NY * BCy * sizeof(float2);  // also a column item's output
-  const size_t sbm = in_rows > in_cols ? in_rows : in_cols;
+  const size_t rows = (size_t)RPI * NX * sizeof(float2);     // transpose block / output of a row item
+  const size_t cols = (size_t)NY * BCy * sizeof(float2);     // a column band
+  size_t sbm = in_rows > rows ? in_rows : rows;
+  sbm = sbm > cols ? sbm : cols;
   stage_bytes = (sbm + 1023) / 1024 * 1024;
-  const size_t fl = (size_t)p.stage_rows * (NX + 2 * kStagePad) * sizeof(float);
-  const size_t rows = (size_t)(kThreads / N1x) * N2x * (N1x + 1) * sizeof(float2);
-  const size_t cols = (size_t)N2y * (N1y * BCy + (BCy < 16 ? BCy : 0)) * sizeof(float2);
-  size_t x = fl > rows ? fl : rows;
-  x = x > cols ? x : cols;
-  xbuf_bytes = (x + 15) / 16 * 16;
-  total = 2 * stage_bytes + xbuf_bytes + (size_t)(NX + NY) * sizeof(float2);  // + twiddle tables
+  total = kStages * stage_bytes + (size_t)(2 * NX + NY) * sizeof(float2);
 }
 
 template <int NX, int NY>
 size_t smem_for(const Plan& p) {
-  size_t sb, xb, total;
-  smem_layout<NX, NY>(p, sb, xb, total);
+  size_t sb, total;
+  smem_layout<NX, NY>(p, sb, total);
   return total;
 }
 
 template <int NX, int NY, bool FW>
 cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, const void* tmap, const void* tmap_inter,
                       int num_sms, cudaStream_t s) {
-  size_t sb, xbb, smem;
-  smem_layout<NX, NY>(p, sb, xbb, smem);
+  size_t sb, smem;
+  smem_layout<NX, NY>(p, sb, smem);
   LateralParams lp = lp_in;
   lp.stage_bytes = (int)sb;
-  lp.xbuf_bytes = (int)xbb;
   cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -84,7 +84,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
     const void* src;
     size_t n;
   } ups[] = {
-      {p.off_xtab, p.xtab.data(), sizeof(TapX) * p.xtab.size()},
+      {p.off_xtab, p.xtab.data(), sizeof(Tap) * p.xtab.size()},
       {p.off_ytab, p.ytab.data(), sizeof(Tap) * p.ytab.size()},
       {p.off_cx, p.cx.data(), sizeof(float2) * p.cx.size()},
       {p.off_cy, p.cy.data(), sizeof(float2) * p.cy.size()},
@@ -112,7 +112,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   lp.nx = p.nx; lp.ny = p.ny; lp.nl = p.nl;
   lp.x0 = p.x0; lp.y0 = p.y0; lp.wx = p.wx; lp.wy = p.wy;
   lp.wxp = p.wxp; lp.ntx = p.ntx;
-  lp.xtab = (const TapX*)(ws + p.off_xtab);
+  lp.xtab = (const Tap*)(ws + p.off_xtab);
   lp.ytab = (const Tap*)(ws + p.off_ytab);
   lp.cx = (const float2*)(ws + p.off_cx);
   lp.cy = (const float2*)(ws + p.off_cy);
@@ -126,7 +126,6 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   lp.sch = p.sch;
   lp.stage_rows = p.stage_rows;
   lp.stage_bytes = 0;
-  lp.xbuf_bytes = 0;
   e = launch_lateral_with(p, lp, tmap, tmap_inter, g_num_sms[dev], s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("lateral kernel launch: ") + cudaGetErrorString(e));
 

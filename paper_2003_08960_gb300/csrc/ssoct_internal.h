@@ -12,7 +12,6 @@
 namespace ssoct {
 
 constexpr int kThreads = 256;          // threads of a lateral-stage CTA (two CTAs per SM)
-constexpr int kStagePad = 4;           // floats of zero padding on each side of a staged input row
 constexpr int kTile = 32;              // pixels per sweep-axis tile (one x-run)
 
 // FFT length N = N1 * N2 as the kernels split it: an N2-point DFT per thread,
@@ -30,17 +29,6 @@ struct __align__(16) Tap {
   float w0;
   float w1;
   float pad;
-};
-
-// x tap of Eq. 5 against a staged input row padded with zeros on both sides:
-// value = row[base] + w1 * (row[base + 1] - row[base]), base in [-1, n-1]; a tap
-// outside the frame lands on a zero pad (base = -1, w1 = 0 when both do).  The
-// column's input chirp of Eq. 6 (centring phase included) rides along, so one
-// 16-byte load serves the pixel.
-struct __align__(16) TapX {
-  int base;
-  float w1;
-  float cre, cim;
 };
 
 // Device work-queue counters of the lateral kernel (zeroed before each launch).
@@ -110,7 +98,7 @@ struct LateralParams {
   int x0, y0, wx, wy;      // window
   int wxp;                 // scratch row pitch (complex elements)
   int ntx;                 // sweep-axis tiles per window row
-  const TapX* xtab;        // [nl][nx]
+  const Tap* xtab;         // [nl][nx]
   const Tap* ytab;         // [nl][ny]
   const float2* cx;        // [nx] input chirp incl. centring phase
   const float2* cy;        // [ny]
@@ -124,7 +112,6 @@ struct LateralParams {
   LateralSchedule sch;
   int stage_rows;          // input rows staged per row item (max over items)
   int stage_bytes;         // bytes of one shared-memory stage buffer (set at launch)
-  int xbuf_bytes;          // bytes of the shared-memory exchange buffer (set at launch)
 };
 
 struct AxialParams {
@@ -157,8 +144,7 @@ struct Plan {
   double kre, kim;          // prefactor K
   double alpha;             // d^2 / (lambda_1 z) = |K|
   // host tables
-  std::vector<TapX> xtab;
-  std::vector<Tap> ytab;
+  std::vector<Tap> xtab, ytab;
   std::vector<float2> cx, cy, ox, oy, twx, twy, twl;
   // geometry of the device work
   int n1x, n2x, n1y, n2y, n1l, n2l;

@@ -62,24 +62,6 @@ Tap make_tap(int i, int n, double s) {
   return t;
 }
 
-// The same tap in the padded-row form the lateral kernel reads (TapX).
-TapX make_tap_x(int i, int n, double s) {
-  const double c = n / 2.0;
-  const double u = c + (i - c) * s;
-  const double fl = std::floor(u);
-  const long i0 = (long)fl;
-  TapX t;
-  if (i0 >= -1 && i0 <= n - 1) {
-    t.base = (int)i0;
-    t.w1 = (float)(u - fl);
-  } else {
-    t.base = -1;
-    t.w1 = 0.f;
-  }
-  t.cre = t.cim = 0.f;  // filled with the input chirp by the plan
-  return t;
-}
-
 // Input chirp of Eq. 6 times the centring phase along one axis of length n:
 // exp(-i pi [(k - n/2)^2 alpha + k]); alpha = d^2 / (lambda_1 z).  With it the
 // centred sum over (k - n/2)(m - n/2) / n becomes a plain DFT over k m / n.
@@ -247,16 +229,11 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.ytab.resize((size_t)nlambda * ny);
   for (int t = 0; t < nlambda; ++t) {
     const double s = lambda_m[t] / p.lambda1;
-    for (int i = 0; i < nx; ++i) p.xtab[(size_t)t * nx + i] = make_tap_x(i, nx, s);
+    for (int i = 0; i < nx; ++i) p.xtab[(size_t)t * nx + i] = make_tap(i, nx, s);
     for (int j = 0; j < ny; ++j) p.ytab[(size_t)t * ny + j] = make_tap(j, ny, s);
   }
   // Eq. 6 chirps.  alpha x (k - n/2)^2 is the chirp phase / pi.
   p.cx = input_chirp(nx, p.alpha);
-  for (int t = 0; t < nlambda; ++t)
-    for (int i = 0; i < nx; ++i) {
-      p.xtab[(size_t)t * nx + i].cre = p.cx[i].x;
-      p.xtab[(size_t)t * nx + i].cim = p.cx[i].y;
-    }
   p.cy = input_chirp(ny, p.alpha);
   p.ox = output_chirp(nx, p.alpha, p.x0, p.wx);
   {
@@ -312,7 +289,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, kAlign); return o; };
   p.off_ctr = take(sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)nlambda);
-  p.off_xtab = take(sizeof(TapX) * p.xtab.size());
+  p.off_xtab = take(sizeof(Tap) * p.xtab.size());
   p.off_ytab = take(sizeof(Tap) * p.ytab.size());
   p.off_cx = take(sizeof(float2) * nx);
   p.off_cy = take(sizeof(float2) * ny);
@@ -364,7 +341,7 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(&p, e, "cudaDeviceGetAttribute");
   char* ws = (char*)dev_ptr;
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
-      {p.off_xtab, p.xtab.data(), sizeof(TapX) * p.xtab.size()},
+      {p.off_xtab, p.xtab.data(), sizeof(Tap) * p.xtab.size()},
       {p.off_ytab, p.ytab.data(), sizeof(Tap) * p.ytab.size()},
       {p.off_cx, p.cx.data(), sizeof(float2) * p.cx.size()},
       {p.off_cy, p.cy.data(), sizeof(float2) * p.cy.size()},
@@ -442,7 +419,7 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
   lp.nx = p.nx; lp.ny = p.ny; lp.nl = p.nl;
   lp.x0 = p.x0; lp.y0 = p.y0; lp.wx = p.wx; lp.wy = p.wy;
   lp.wxp = p.wxp; lp.ntx = p.ntx;
-  lp.xtab = (const TapX*)(ws + p.off_xtab);
+  lp.xtab = (const Tap*)(ws + p.off_xtab);
   lp.ytab = (const Tap*)(ws + p.off_ytab);
   lp.cx = (const float2*)(ws + p.off_cx);
   lp.cy = (const float2*)(ws + p.off_cy);
