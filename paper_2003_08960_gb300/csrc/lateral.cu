@@ -121,6 +121,10 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_reads() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // every committed group of this thread has finished writing global memory
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// every committed group but the most recent one has finished writing
+__device__ __forceinline__ void bulk_wait_all_but_last() {
+  asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
+}
 // Order this thread's generic-proxy shared-memory writes before later async-proxy
 // (TMA) reads of them, and generic / async global accesses against each other.
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -338,13 +342,26 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
   const unsigned long long pol_last = policy_evict_last();
   const unsigned long long pol_first = policy_evict_first();
   auto publish = [&](int kind, int f) { red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u); };
-  // publish items whose TMA writes are complete
+  // publish items whose TMA writes are complete (pend_* in commit order, one
+  // bulk group per item)
   auto flush = [&]() {
     if (pend_n) {
       bulk_wait_all();
       fence_proxy_async_global();
       for (int i = 0; i < pend_n; ++i) publish(pend_kind[i], pend_f[i]);
       pend_n = 0;
+    }
+  };
+  // publish all but the newest: the older groups were issued at least one item
+  // ago, so this rarely waits
+  auto flush_older = [&]() {
+    if (pend_n >= 2) {
+      bulk_wait_all_but_last();
+      fence_proxy_async_global();
+      for (int i = 0; i + 1 < pend_n; ++i) publish(pend_kind[i], pend_f[i]);
+      pend_kind[0] = pend_kind[pend_n - 1];
+      pend_f[0] = pend_f[pend_n - 1];
+      pend_n = 1;
     }
   };
   // free the buffers whose TMA stores have read them
@@ -491,6 +508,8 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
     // the next ticket, requested once this one is handed over (its round trip
     // overlaps the wait for the next free buffer)
     t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
+    service();
+    flush_older();
   }
   // drain: publish what is still in flight
   const unsigned long long t0 = global_timer_ns();
