@@ -383,24 +383,32 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
     if constexpr (FW) {
       const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
       if (st_kind[b] == kRowItem) {
+        // eight contiguous rows: quick to write, and column items of this frame
+        // are waiting for them, so publish as soon as they are written
         float2* dst = p.scratch + ((size_t)(st_f[b] % p.sch.slots) * NY + st_item[b] * RPI) * p.wxp;
 #pragma unroll 1
         for (int r = 0; r < RPI; ++r)
           tma_store_1d(dst + (size_t)r * p.wxp, buf + (size_t)r * NX * sizeof(float2), (unsigned)(NX * sizeof(float2)),
                        pol_last);
+        bulk_commit();
+        flush();  // every group, this one included
+        publish(kRowItem, st_f[b]);
+        st_kind[b] = -1;
       } else {
+        // a column band: many short rows, slower to write; only the reuse of its
+        // scratch slot (several frames later) waits for it, so publish lazily
         const int b0 = st_item[b] * BC;
         const int x = 2 * (((b0 / kTile) * p.nl + st_f[b]) * kTile + (b0 % kTile));
 #pragma unroll
         for (int i = 0; i < NY / BOX_ROWS; ++i)
           tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
+        bulk_commit();
+        if (pend_n == kStages) flush();
+        pend_kind[pend_n] = st_kind[b];
+        pend_f[pend_n] = st_f[b];
+        ++pend_n;
+        st_storing[b] = true;
       }
-      bulk_commit();
-      if (pend_n == kStages) flush();
-      pend_kind[pend_n] = st_kind[b];
-      pend_f[pend_n] = st_f[b];
-      ++pend_n;
-      st_storing[b] = true;
     } else {
       publish(st_kind[b], st_f[b]);
       st_kind[b] = -1;
