@@ -108,6 +108,19 @@ def _dist():
     return world, rank, local
 
 
+def aggregate(local_ms: float, voxels_per_rank: int, world: int, dist=None, device="cpu"):
+    """Whole-job throughput: every rank reconstructs its own volumes, the job's
+    time per step is the slowest rank's, value = all ranks' voxels / that time.
+    Returns (max ms over ranks, Gvoxel/s)."""
+    ms = float(local_ms)
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * voxels_per_rank / (ms * 1e-3) / 1e9
+
+
 def oracle_rate(w, n_frames: int):
     """FP64 oracle (as it stands) on a gate of the first n_frames frames of the
     workload: returns (voxels per second, seconds, threads)."""
@@ -221,15 +234,11 @@ def run_ssoct(args):
     clk = clocks.stop()
     lat_ms /= max(calls, 1)
     ax_ms /= max(calls, 1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     voxels = wx * wy * nl
-    value = world * voxels / (ms * 1e-3) / 1e9
+    ms, value = aggregate(ms, voxels, world, dist if world > 1 else None, device="cuda")
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
-    e2e = _e2e(args, ss, torch, dist, w, h, stream, sp, vol, nl, voxels, world) if not args.no_e2e else None
+    e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
     peak, peak_kind = _peaks()
     lat_bytes = w.nx * w.ny * nl * 2 + voxels * 8
     ax_bytes = voxels * (8 + 4)
@@ -273,43 +282,64 @@ def run_ssoct(args):
         dist.destroy_process_group()
 
 
-def _e2e(args, ss, torch, dist, w, h, stream, sp, vol, nl, voxels, world):
-    """Same metric through the C ABI with host buffers: pinned host frames are
-    pushed into the plan's ring (H2D), the volume is reconstructed and read back
-    to pinned host memory (D2H), all inside the timed region."""
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+def _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world):
+    """Same metric through the C ABI with host buffers: every step pushes its
+    frames from pinned host memory into a plan's ring (H2D), reconstructs the
+    volume and reads it back to pinned host memory (D2H), all inside the timed
+    region.  Two plans (two rings) and three streams let step k's H2D overlap
+    step k-1's reconstruction and step k-2's D2H, as an acquisition pipeline
+    would run; events keep each ring and volume buffer from being reused early."""
+    plans = [plan, ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)]
+    vols = [vol, torch.empty_like(vol)]
     host_frames = torch.from_numpy(w.frames.view(np.int16)).pin_memory()
-    host_vol = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+    host_vols = [torch.empty(vol.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    s_h2d, s_comp, s_d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_h2d = [torch.cuda.Event() for _ in range(2)]
+    ev_comp = [torch.cuda.Event() for _ in range(2)]
+    ev_d2h = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = max(3, min(args.steps, 20))
 
-    def e2e_step():
-        s1 = ss.ssoct_push_frames(h, host_frames.data_ptr(), nl, False, -1, sp)
-        s2 = ss.ssoct_reconstruct_volume(h, vol.data_ptr(), 0, sp)
-        if s1 or s2:
+    def e2e_step(k):
+        i = k % 2
+        h = plans[i].handle
+        if k >= 2:
+            s_h2d.wait_event(ev_comp[i])      # the ring's previous gate has been read
+        if ss.ssoct_push_frames(h, host_frames.data_ptr(), nl, False, -1, s_h2d.cuda_stream):
             raise RuntimeError(ss.ssoct_last_error(h))
-        with torch.cuda.stream(stream):
-            host_vol.copy_(vol, non_blocking=True)
+        ev_h2d[i].record(s_h2d)
+        s_comp.wait_event(ev_h2d[i])
+        if k >= 2:
+            s_comp.wait_event(ev_d2h[i])      # the volume buffer has been read back
+        if ss.ssoct_reconstruct_volume(h, vols[i].data_ptr(), 0, s_comp.cuda_stream):
+            raise RuntimeError(ss.ssoct_last_error(h))
+        ev_comp[i].record(s_comp)
+        s_d2h.wait_event(ev_comp[i])
+        with torch.cuda.stream(s_d2h):
+            host_vols[i].copy_(vols[i], non_blocking=True)
+        ev_d2h[i].record(s_d2h)
 
-    for _ in range(2):
-        e2e_step()
+    for k in range(2):
+        e2e_step(k)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s_h2d)
+    for k in range(2, 2 + e2e_steps):
+        e2e_step(k)
+    s_d2h.wait_stream(s_h2d)
+    s_d2h.wait_stream(s_comp)
+    e1.record(s_d2h)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * voxels / (e2e_ms * 1e-3) / 1e9
-
+    for pl in plans:
+        if ss.ssoct_sync(pl.handle, 0):
+            raise RuntimeError("kernel error: " + ss.ssoct_last_error(pl.handle))
+    e2e_ms, e2e_value = aggregate(e2e_ms, voxels, world, dist if world > 1 else None, device="cuda")
     return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_frames.numel() * 2),
-            "d2h_bytes_per_step": int(host_vol.numel() * 4), "ms_per_step": e2e_ms}
+            "d2h_bytes_per_step": int(host_vols[0].numel() * 4), "ms_per_step": e2e_ms,
+            "pipeline": "2 rings, H2D / reconstruct / D2H on 3 streams"}
 
 
 def _traffic(kernel: str):

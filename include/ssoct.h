@@ -183,6 +183,15 @@ SSOCT_API ssoct_status ssoct_profile(ssoct_plan plan, int enable);
  * pointer may be NULL. */
 SSOCT_API ssoct_status ssoct_profile_read(ssoct_plan plan, double* lateral_ms, double* axial_ms, int* calls);
 
+/* Failure injection for tests of the time-out path.  The next reconstruct calls
+ * on this plan start the lateral kernel's work queue `skip` items in, so the
+ * items that depend on the skipped ones can never start; every device-side wait
+ * gives up after wait_limit_ns (0 = the default of 2 s), the kernels return with
+ * their output incomplete, and ssoct_sync reports SSOCT_ETIMEOUT.  Nothing
+ * faults or hangs, and the device stays usable.  skip = 0, wait_limit_ns = 0
+ * restores normal operation. */
+SSOCT_API ssoct_status ssoct_inject_stall(ssoct_plan plan, unsigned skip, unsigned long long wait_limit_ns);
+
 /* Message for the last non-OK status returned on this plan ("" if none). */
 SSOCT_API const char* ssoct_last_error(ssoct_plan plan);
 

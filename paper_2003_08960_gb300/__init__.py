@@ -103,6 +103,12 @@ def ssoct_sync(plan, stream: int) -> int:
     return _abi.lib().ssoct_sync(plan, C.c_void_p(stream))
 
 
+def ssoct_inject_stall(plan, skip: int, wait_limit_ns: int) -> int:
+    """Test hook: make the next reconstructs skip `skip` work items so that
+    dependent items time out after wait_limit_ns (see include/ssoct.h)."""
+    return _abi.lib().ssoct_inject_stall(plan, skip, wait_limit_ns)
+
+
 def ssoct_profile(plan, enable: bool) -> int:
     return _abi.lib().ssoct_profile(plan, int(bool(enable)))
 

@@ -65,6 +65,7 @@ SIGNATURES = {
     "ssoct_get_cuts": (C.c_int, [ssoct_plan, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssoct_sync": (C.c_int, [ssoct_plan, C.c_void_p]),
+    "ssoct_inject_stall": (C.c_int, [ssoct_plan, C.c_uint, C.c_ulonglong]),
     "ssoct_profile": (C.c_int, [ssoct_plan, C.c_int]),
     "ssoct_profile_read": (C.c_int, [ssoct_plan, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(C.c_int)]),

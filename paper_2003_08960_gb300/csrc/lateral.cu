@@ -438,6 +438,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
     atomicExch(&p.ctr->abort, 1u);
   };
+  const unsigned long long wait_limit = p.wait_ns ? p.wait_ns : kProducerWaitNs;
   // The producer prepares item s (ticket, dependency, descriptor) before its
   // buffer is free, and only the copy issue waits for the buffer.  A CTA holds
   // at most one unstarted, unpublished ticket; the lowest unfinished ticket is
@@ -467,7 +468,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
           service();
           release_reads();
           flush();
-          if (*(volatile unsigned*)&p.ctr->abort || global_timer_ns() - t0 > kProducerWaitNs) {
+          if (*(volatile unsigned*)&p.ctr->abort || global_timer_ns() - t0 > wait_limit) {
             give_up();
             kind = kEndItem;
             break;
@@ -491,7 +492,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
         service();
         if (st_kind[b] >= 0 && st_storing[b]) release_reads();
         if (st_kind[b] >= 0) flush();
-        if (st_kind[b] >= 0 && global_timer_ns() - t0 > kProducerWaitNs) {
+        if (st_kind[b] >= 0 && global_timer_ns() - t0 > wait_limit) {
           give_up();
           kind = kEndItem;  // the buffer's old item is lost; consumers still get an end mark
           break;
@@ -543,7 +544,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
 #pragma unroll
     for (int i = 0; i < kStages; ++i) busy |= st_kind[i] >= 0;
     if (!busy) break;
-    if (global_timer_ns() - t0 > kProducerWaitNs) {
+    if (global_timer_ns() - t0 > wait_limit) {
       give_up();
       break;
     }
@@ -587,7 +588,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   int b = 0;
   unsigned use = 0;  // completions of full[b] seen so far, per pass over the buffers
   for (;;) {
-    const bool ok = mbar_wait(&full_bar[b], use & 1u, p.ctr, kConsumerWaitNs);
+    // consumers wait longer than the producer, which gives up first and hands
+    // them an end mark
+    const bool ok = mbar_wait(&full_bar[b], use & 1u, p.ctr, p.wait_ns ? 2 * p.wait_ns : kConsumerWaitNs);
     // all consumers agree, and the previous item is finished everywhere
     if (consumers_sync_or(!ok)) break;
     const Desc d = desc[b];

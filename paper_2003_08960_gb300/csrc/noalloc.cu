@@ -126,6 +126,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   lp.sch = p.sch;
   lp.stage_rows = p.stage_rows;
   lp.stage_bytes = 0;
+  lp.wait_ns = p.wait_ns;
   e = launch_lateral_with(p, lp, tmap, tmap_inter, g_num_sms[dev], s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("lateral kernel launch: ") + cudaGetErrorString(e));
 

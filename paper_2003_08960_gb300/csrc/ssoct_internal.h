@@ -112,6 +112,7 @@ struct LateralParams {
   LateralSchedule sch;
   int stage_rows;          // input rows staged per row item (max over items)
   int stage_bytes;         // bytes of one shared-memory stage buffer (set at launch)
+  unsigned long long wait_ns;  // limit of every device-side wait (0 = default)
 };
 
 struct AxialParams {
@@ -165,6 +166,9 @@ struct Plan {
   int ring_head = 0;        // next ring slot to write
   long long next_seq = -1;
   std::string last_error;
+  // failure injection (ssoct_inject_stall)
+  unsigned inject_skip = 0;
+  unsigned long long wait_ns = 0;
   // stage timing (ssoct_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> events;  // 3 per recorded call: start, after lateral, after axial

@@ -432,8 +432,16 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
   lp.cols_done = lp.rows_done + p.nl;
   lp.sch = p.sch;
   lp.stage_rows = p.stage_rows;
+  lp.wait_ns = p.wait_ns;
   cudaError_t e = cudaMemsetAsync(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "counter reset");
+  if (p.inject_skip) {
+    // start the ticket counter past the first items (ssoct_inject_stall)
+    e = cudaMemcpyAsync(ws + p.off_ctr, &p.inject_skip, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "stall injection");
+    e = cudaStreamSynchronize(s);  // the host value must outlive the copy
+    if (e != cudaSuccess) return cuda_fail(&p, e, "stall injection");
+  }
   cudaEvent_t* ev = nullptr;
   if (p.profiling) {
     if (p.events_used + 3 > p.events.size()) {
@@ -513,6 +521,13 @@ ssoct_status ssoct_sync(ssoct_plan h, void* stream) {
     cudaMemset(p.ws + p.off_ctr, 0, sizeof(Counters));
     return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue");
   }
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_inject_stall(ssoct_plan h, unsigned skip, unsigned long long wait_limit_ns) {
+  if (!h) return SSOCT_EINVAL;
+  h->p.inject_skip = skip;
+  h->p.wait_ns = wait_limit_ns;
   return SSOCT_OK;
 }
 

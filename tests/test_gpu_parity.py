@@ -170,3 +170,24 @@ def test_paper_size_1024x1024x256(ss):
     plan, vol, cplx, ref = _run(ss, w, method="fft")
     err = _check(vol, cplx, ref)
     print(f"1024x1024x256 complex rel L2 = {err:.3e}")
+
+
+def test_wait_timeout_is_reported_and_device_recovers(ss):
+    """Failure path of the bounded device waits: skipping the first work item
+    leaves the column items of frame 0 waiting for a row item that never runs;
+    they give up after 50 ms, the kernels return, ssoct_sync reports
+    SSOCT_ETIMEOUT, and the next normal call reproduces the volume exactly."""
+    w = synth.workload("tiny_64x64x32")
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    f = _dev(w.frames)
+    ref = plan.reconstruct(f)
+    plan.sync()
+    stream = torch.cuda.current_stream().cuda_stream
+    assert ss.ssoct_inject_stall(plan.handle, 1, 50_000_000) == ss.SSOCT_OK
+    plan.reconstruct(f)
+    assert ss.ssoct_sync(plan.handle, stream) == ss.SSOCT_ETIMEOUT
+    assert "gave up" in ss.ssoct_last_error(plan.handle)
+    assert ss.ssoct_inject_stall(plan.handle, 0, 0) == ss.SSOCT_OK
+    again = plan.reconstruct(f)
+    plan.sync()
+    assert torch.equal(again, ref)
