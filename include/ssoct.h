@@ -159,6 +159,21 @@ SSOCT_API ssoct_status ssoct_reconstruct_frames(ssoct_plan plan, const uint16_t*
 SSOCT_API ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan plan, const uint16_t* frames_dev,
                                                         float* vol_dev, void* complex_dev, void* stream);
 
+/* Sliding gates (the paper renders volumes faster than sweeps arrive by
+ * sliding the rectangular gate of Eq. 7 along the frame stream).  Requires a
+ * periodic sweep: frame i of the stream pushed since the gate (re)started was
+ * taken at lambda_m[i mod nlambda], so ring slot r always holds wavelength r.
+ * Reconstructs the gate of the last nlambda pushed frames; only frames pushed
+ * since the previous sliding call (at most nlambda) go through the lateral
+ * stage (Eq. 5 + Eq. 6), their holograms being kept in the sweep-axis
+ * intermediate, and the transform over the gate (Eq. 7) runs in slot order.
+ * Rotating the gate only multiplies V by exp(2 pi i q s / nlambda), so vol_dev
+ * (|V|^2) is that of the gate in time order; complex_dev (NULL or [nlambda][wy]
+ * [wx]) receives V in slot order.  Any other reconstruct call on the plan
+ * overwrites the intermediate, and the next sliding call redoes all nlambda
+ * frames.  ENOTREADY before nlambda frames. */
+SSOCT_API ssoct_status ssoct_reconstruct_sliding(ssoct_plan plan, float* vol_dev, void* complex_dev, void* stream);
+
 /* The three orthogonal cuts of a volume written by a reconstruct call with this
  * plan (text after Eq. 7; Fig. 5): xy[wy][wx] = P(x, y, z0), xz[nlambda][wx] =
  * P(x, y0, z), yz[nlambda][wy] = P(x0, y, z), coordinates in window pixels and

@@ -86,6 +86,11 @@ def ssoct_reconstruct_frames(plan, frames_ptr: int, vol_ptr: int, complex_ptr: i
                                                C.c_void_p(complex_ptr or None), C.c_void_p(stream))
 
 
+def ssoct_reconstruct_sliding(plan, vol_ptr: int, complex_ptr: int, stream: int) -> int:
+    return _abi.lib().ssoct_reconstruct_sliding(plan, C.c_void_p(vol_ptr), C.c_void_p(complex_ptr or None),
+                                                C.c_void_p(stream))
+
+
 def ssoct_reconstruct_frames_noalloc(plan, frames_ptr: int, vol_ptr: int, complex_ptr: int, stream: int) -> int:
     """ssoct_reconstruct_frames without any device allocation (scratch in a fixed
     64 MiB device array inside the library); the plan needs no workspace."""
@@ -227,6 +232,14 @@ class Plan:
         vol, cplx = out if out is not None else self.empty_volume(complex_out)
         _check(ssoct_reconstruct_volume(self._h, vol.data_ptr(), cplx.data_ptr() if cplx is not None else 0,
                                         _stream_ptr(stream)), self._h, "reconstruct_volume")
+        return (vol, cplx) if complex_out else vol
+
+    def reconstruct_sliding(self, out=None, complex_out: bool = False, stream=None):
+        """Volume of the last nlambda pushed frames of a periodic sweep (sliding
+        gate); only frames pushed since the previous call are transformed."""
+        vol, cplx = out if out is not None else self.empty_volume(complex_out)
+        _check(ssoct_reconstruct_sliding(self._h, vol.data_ptr(), cplx.data_ptr() if cplx is not None else 0,
+                                         _stream_ptr(stream)), self._h, "reconstruct_sliding")
         return (vol, cplx) if complex_out else vol
 
     def cuts(self, vol, x0: int, y0: int, z0: int, stream=None):

@@ -61,6 +61,7 @@ SIGNATURES = {
     "ssoct_push_frames": (C.c_int, [ssoct_plan, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p]),
     "ssoct_reconstruct_volume": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssoct_reconstruct_frames": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ssoct_reconstruct_sliding": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssoct_reconstruct_frames_noalloc": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssoct_get_cuts": (C.c_int, [ssoct_plan, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

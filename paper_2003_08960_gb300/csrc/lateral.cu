@@ -37,7 +37,7 @@ constexpr unsigned long long kConsumerWaitNs = 4000000000ull;   // longer: the p
 enum : int { kRowItem = 0, kColItem = 1, kEndItem = 2 };
 
 struct Desc {
-  int kind, f, item, jlo, nrows;
+  int kind, f, item, jlo, nrows, slot;  // slot: wavelength / intermediate index of frame f
 };
 
 // ---------------------------------------------------------------- mbarrier / TMA
@@ -308,7 +308,7 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
     const int kxw = d.item * BC + b;
     if (kxw < p.wx) {
       const unsigned long long pol_first = policy_evict_first();
-      float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)d.f * kTile + (kxw % kTile);
+      float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)d.slot * kTile + (kxw % kTile);
       const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
       static_for<0, N2 / N1>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -413,7 +413,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
         // a column band: many short rows, slower to write; only the reuse of its
         // scratch slot (several frames later) waits for it, so publish lazily
         const int b0 = st_item[b] * BC;
-        const int x = 2 * (((b0 / kTile) * p.nl + st_f[b]) * kTile + (b0 % kTile));
+        const int x = 2 * (((b0 / kTile) * p.nl + (p.tab0 + st_f[b]) % p.nl) * kTile + (b0 % kTile));
 #pragma unroll
         for (int i = 0; i < NY / BOX_ROWS; ++i)
           tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
@@ -478,9 +478,10 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       }
     }
     fence_proxy_async_global();  // the acquired data is read by TMA (async proxy)
-    Desc d{kind, f, item, 0, 0};
+    const int slot = (p.tab0 + f) % p.nl;
+    Desc d{kind, f, item, 0, 0, slot};
     if (kind == kRowItem) {
-      const Tap* yt = p.ytab + (size_t)f * NY;
+      const Tap* yt = p.ytab + (size_t)slot * NY;
       d.jlo = yt[item * RPI].base;
       d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
     }
@@ -501,7 +502,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
     }
     // 3. hand over
     if (kind == kEndItem) {
-      desc[b] = Desc{kEndItem, 0, 0, 0, 0};
+      desc[b] = Desc{kEndItem, 0, 0, 0, 0, 0};
       mbar_arrive(&full_bar[b]);
       break;
     }
@@ -515,8 +516,8 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       mbar_arrive_tx(&full_bar[b], bytes + tap_bytes + yt_bytes + cy_bytes);
       const int fr = (p.ring_start + f) % p.nl;
       tma_load_1d(buf, p.frames + ((size_t)fr * NY + d.jlo) * NX, bytes, &full_bar[b]);
-      tma_load_1d(buf + tap_off, p.xtab + (size_t)f * NX, tap_bytes, &full_bar[b]);
-      tma_load_1d(buf + tap_off + tap_bytes, p.ytab + (size_t)f * NY + item * RPI, yt_bytes, &full_bar[b]);
+      tma_load_1d(buf + tap_off, p.xtab + (size_t)slot * NX, tap_bytes, &full_bar[b]);
+      tma_load_1d(buf + tap_off + tap_bytes, p.ytab + (size_t)slot * NY + item * RPI, yt_bytes, &full_bar[b]);
       tma_load_1d(buf + tap_off + tap_bytes + yt_bytes, p.cy + item * RPI, cy_bytes, &full_bar[b]);
     } else {
       mbar_arrive_tx(&full_bar[b], (unsigned)(NY * BC * sizeof(float2)));

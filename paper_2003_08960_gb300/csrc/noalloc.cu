@@ -109,6 +109,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   LateralParams lp;
   lp.frames = frames_dev;
   lp.ring_start = 0;
+  lp.tab0 = 0;
   lp.nx = p.nx; lp.ny = p.ny; lp.nl = p.nl;
   lp.x0 = p.x0; lp.y0 = p.y0; lp.wx = p.wx; lp.wy = p.wy;
   lp.wxp = p.wxp; lp.ntx = p.ntx;

@@ -92,8 +92,9 @@ struct LateralSchedule {
 
 // Everything the lateral kernel (rescale + chirp + row FFT, column FFT) reads.
 struct LateralParams {
-  const uint16_t* frames;  // gate frame t at frames + ((ring_start + t) % nl) * nx * ny
+  const uint16_t* frames;  // batch frame f at frames + ((ring_start + f) % nl) * nx * ny
   int ring_start;
+  int tab0;                // batch frame f has wavelength / intermediate index (tab0 + f) % nl
   int nx, ny, nl;
   int x0, y0, wx, wy;      // window
   int wxp;                 // scratch row pitch (complex elements)
@@ -165,6 +166,8 @@ struct Plan {
   long long pushed = 0;     // frames in the current gate (capped at nl)
   int ring_head = 0;        // next ring slot to write
   long long next_seq = -1;
+  long long stream_count = 0;  // frames pushed since the gate (re)started, uncapped
+  long long lat_upto = -1;     // sliding gates: stream index up to which the intermediate holds holograms
   std::string last_error;
   // failure injection (ssoct_inject_stall)
   unsigned inject_skip = 0;

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include <cuda.h>
@@ -358,6 +359,8 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
   e = cudaMemset(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl);
   if (e != cudaSuccess) return cuda_fail(&p, e, "counter reset");
   p.ws = ws;
+  p.stream_count = 0;
+  p.lat_upto = -1;
   if (!encode_scratch_map(p) || !encode_inter_map_at(p, p.ws + p.off_inter, p.tmap_inter)) {
     p.ws = nullptr;
     return fail(&p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the scratch ring or the intermediate");
@@ -380,6 +383,8 @@ ssoct_status ssoct_push_frames(ssoct_plan h, const uint16_t* frames, int n, int 
       // a drop: the current gate can no longer hold consecutive frames
       p.pushed = 0;
       p.ring_head = 0;
+      p.stream_count = 0;
+      p.lat_upto = -1;
       st = SSOCT_EDROPPED;
     }
     p.next_seq = first_seq + n;
@@ -404,18 +409,20 @@ ssoct_status ssoct_push_frames(ssoct_plan h, const uint16_t* frames, int n, int 
     p.pushed += run;
   }
   if (p.pushed > p.nl) p.pushed = p.nl;
+  p.stream_count += n;
   if (st != SSOCT_OK) p.last_error = "frame sequence skipped; gate restarted";
   return st;
 }
 
-static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, float* vol, void* cplx,
-                               cudaStream_t s) {
-  if (!vol || ((uintptr_t)vol % 16) || ((uintptr_t)cplx % 16))
-    return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
+// Lateral-kernel parameters of a plan over its workspace: batch frame f is read
+// from ring slot (ring_start + f) % nl and has wavelength / intermediate index
+// (tab0 + f) % nl.  The schedule covers all nl frames.
+static LateralParams lateral_params(const Plan& p, const uint16_t* frames, int ring_start, int tab0) {
   char* ws = p.ws;
   LateralParams lp;
   lp.frames = frames;
   lp.ring_start = ring_start;
+  lp.tab0 = tab0;
   lp.nx = p.nx; lp.ny = p.ny; lp.nl = p.nl;
   lp.x0 = p.x0; lp.y0 = p.y0; lp.wx = p.wx; lp.wy = p.wy;
   lp.wxp = p.wxp; lp.ntx = p.ntx;
@@ -432,7 +439,15 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
   lp.cols_done = lp.rows_done + p.nl;
   lp.sch = p.sch;
   lp.stage_rows = p.stage_rows;
+  lp.stage_bytes = 0;
   lp.wait_ns = p.wait_ns;
+  return lp;
+}
+
+// Reset the work counters and launch the lateral kernel (with the stage events
+// of ssoct_profile); *ev receives the event slots of this call, if profiling.
+static ssoct_status launch_lateral_pass(Plan& p, const LateralParams& lp, cudaStream_t s, cudaEvent_t** ev) {
+  char* ws = p.ws;
   cudaError_t e = cudaMemsetAsync(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "counter reset");
   if (p.inject_skip) {
@@ -442,7 +457,7 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
     e = cudaStreamSynchronize(s);  // the host value must outlive the copy
     if (e != cudaSuccess) return cuda_fail(&p, e, "stall injection");
   }
-  cudaEvent_t* ev = nullptr;
+  *ev = nullptr;
   if (p.profiling) {
     if (p.events_used + 3 > p.events.size()) {
       for (int i = 0; i < 3; ++i) {
@@ -452,15 +467,20 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
         p.events.push_back(x);
       }
     }
-    ev = p.events.data() + p.events_used;
+    *ev = p.events.data() + p.events_used;
     p.events_used += 3;
-    cudaEventRecord(ev[0], s);
+    cudaEventRecord((*ev)[0], s);
   }
   e = launch_lateral(p, lp, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "lateral kernel launch");
-  if (ev) cudaEventRecord(ev[1], s);
+  if (*ev) cudaEventRecord((*ev)[1], s);
+  return SSOCT_OK;
+}
+
+static ssoct_status launch_axial_pass(Plan& p, float* vol, void* cplx, cudaStream_t s, cudaEvent_t* ev) {
+  char* ws = p.ws;
   AxialParams ap;
-  ap.inter = lp.inter;
+  ap.inter = (const float2*)(ws + p.off_inter);
   ap.vol = vol;
   ap.cplx = (float2*)cplx;
   ap.twl = (const float2*)(ws + p.off_twl);
@@ -469,10 +489,22 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
   ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
   ap.power_scale = (float)(p.alpha * p.alpha);
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
-  e = launch_axial(p, ap, s);
+  cudaError_t e = launch_axial(p, ap, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "axial kernel launch");
   if (ev) cudaEventRecord(ev[2], s);
   return SSOCT_OK;
+}
+
+static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, float* vol, void* cplx,
+                               cudaStream_t s) {
+  if (!vol || ((uintptr_t)vol % 16) || ((uintptr_t)cplx % 16))
+    return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
+  const LateralParams lp = lateral_params(p, frames, ring_start, 0);
+  p.lat_upto = -1;  // the intermediate no longer holds the sliding-gate holograms
+  cudaEvent_t* ev = nullptr;
+  ssoct_status st = launch_lateral_pass(p, lp, s, &ev);
+  if (st != SSOCT_OK) return st;
+  return launch_axial_pass(p, vol, cplx, s, ev);
 }
 
 ssoct_status ssoct_reconstruct_volume(ssoct_plan h, float* vol_dev, void* complex_dev, void* stream) {
@@ -492,6 +524,47 @@ ssoct_status ssoct_reconstruct_frames(ssoct_plan h, const uint16_t* frames_dev, 
   if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
   if (!frames_dev || ((uintptr_t)frames_dev % 16)) return fail(&p, SSOCT_EINVAL, "frames NULL or not 16-byte aligned");
   return run_volume(p, frames_dev, 0, vol_dev, complex_dev, (cudaStream_t)stream);
+}
+
+ssoct_status ssoct_reconstruct_sliding(ssoct_plan h, float* vol_dev, void* complex_dev, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
+  if (p.stream_count < p.nl) return fail(&p, SSOCT_ENOTREADY, "fewer than nlambda frames pushed");
+  if (!vol_dev || ((uintptr_t)vol_dev % 16) || ((uintptr_t)complex_dev % 16))
+    return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  // holograms still missing for the gate of the last nl frames: stream frames
+  // [first, stream_count), in ring slots first % nl onwards
+  const long long first = std::max(p.lat_upto, p.stream_count - p.nl);
+  const int k = (int)(p.stream_count - first);
+  cudaEvent_t* ev = nullptr;
+  if (k > 0) {
+    const int slot0 = (int)(first % p.nl);
+    LateralParams lp = lateral_params(p, (const uint16_t*)(p.ws + p.off_ring), slot0, slot0);
+    lp.sch.nl = k;
+    lp.sch.lag = k >= 3 ? 2 : k - 1;
+    lp.sch.slots = lp.sch.lag + 4;  // never more than the plan's ring of scratch slots
+    ssoct_status st = launch_lateral_pass(p, lp, s, &ev);
+    if (st != SSOCT_OK) return st;
+  }
+  p.lat_upto = p.stream_count;
+  if (k == 0 && p.profiling) {
+    // keep the profile's three events per call: an empty lateral interval
+    cudaEvent_t* e0 = nullptr;
+    if (p.events_used + 3 > p.events.size())
+      for (int i = 0; i < 3; ++i) {
+        cudaEvent_t x;
+        if (cudaEventCreate(&x) != cudaSuccess) return fail(&p, SSOCT_ECUDA, "event create");
+        p.events.push_back(x);
+      }
+    e0 = p.events.data() + p.events_used;
+    p.events_used += 3;
+    cudaEventRecord(e0[0], s);
+    cudaEventRecord(e0[1], s);
+    ev = e0;
+  }
+  return launch_axial_pass(p, vol_dev, complex_dev, s, ev);
 }
 
 ssoct_status ssoct_get_cuts(ssoct_plan h, const float* vol_dev, int x0, int y0, int z0, float* xy,
