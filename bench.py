@@ -184,7 +184,8 @@ def run_ssoct(args):
         w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=3 + rank)
     else:
         w = synth.workload(WORKLOAD, seed=3 + rank)
-    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    flags = ss.SSOCT_FLAG_TC_AXIAL if args.tc_axial else 0
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=flags)
     h = plan.handle
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
@@ -237,11 +238,12 @@ def run_ssoct(args):
     voxels = wx * wy * nl
     ms, value = aggregate(ms, voxels, world, dist if world > 1 else None, device="cuda")
 
+    peak, peak_kind = _peaks()
+    tc = None if (args.tc_axial or args.no_e2e) else _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak)
     sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if not args.no_e2e else None
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
     e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
-    peak, peak_kind = _peaks()
     lat_bytes = w.nx * w.ny * nl * 2 + voxels * 8
     ax_bytes = voxels * (8 + 4)
     kernels = {
@@ -251,7 +253,7 @@ def run_ssoct(args):
     for k in kernels.values():
         k["frac"] = k["GBps"] / peak
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    traffic = _traffic(dom)
+    traffic = _traffic("axial_tc" if (args.tc_axial and dom == "axial") else dom)
     whole_bytes = lat_bytes + ax_bytes
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -260,7 +262,8 @@ def run_ssoct(args):
         "data": "synthetic (seeded point scatterers, 12-bit, Gaussian read noise)",
         "config": {"workload": f"{w.nx}x{w.ny}x{nl} sweep, uint16 frames resident in HBM, full window, "
                                "|V|^2 volume + 3 cuts per step",
-                   "window": [0, 0, wx, wy], "form": "fp32 (paper order)",
+                   "window": [0, 0, wx, wy],
+                   "form": "tensor-core axial (bf16 hi+lo, fp32 accumulate)" if args.tc_axial else "fp32 (paper order)",
                    "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["GBps"], "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
@@ -271,6 +274,7 @@ def run_ssoct(args):
         "kernels": kernels,
         "e2e": e2e,
         "sliding": sliding,
+        "tc_axial": tc,
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
@@ -388,6 +392,47 @@ def _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream, step_frames
             "paper": "38 volumes/s (TITAN Xp, sliding 256-frame gate, 512 frames/s)"}
 
 
+def _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak):
+    """The same step with the axial DFT on the tensor cores (SSOCT_FLAG_TC_AXIAL),
+    on the same frames; vol holds the FP32 form's volume of those frames, and the
+    relative L2 distance between the two volumes is reported beside the rate."""
+    if w.nlambda != 256:
+        return None
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=ss.SSOCT_FLAG_TC_AXIAL)
+    h, sp = plan.handle, stream.cuda_stream
+    vt, _ = plan.empty_volume()
+
+    def step():
+        if ss.ssoct_reconstruct_frames(h, frames.data_ptr(), vt.data_ptr(), 0, sp):
+            raise RuntimeError(ss.ssoct_last_error(h))
+
+    for _ in range(args.warmup):
+        step()
+    if ss.ssoct_sync(h, sp) != 0:
+        raise RuntimeError(ss.ssoct_last_error(h))
+    ss.ssoct_profile(h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ss.ssoct_sync(h, sp) != 0:
+        raise RuntimeError(ss.ssoct_last_error(h))
+    _, lat_ms, ax_ms, calls = ss.ssoct_profile_read(h)
+    ax_ms /= max(calls, 1)
+    ax_bytes = voxels * (8 + 4)
+    d = (vt.double() - vol.double()).norm() / vol.double().norm()
+    return {"value": voxels / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "axial_ms": ax_ms, "axial_GBps": ax_bytes / (ax_ms * 1e-3) / 1e9,
+            "axial_frac": ax_bytes / (ax_ms * 1e-3) / 1e9 / peak,
+            "rel_l2_vs_fp32_volume": float(d),
+            "form": "axial DFT as two 16-point tcgen05 MMA stages, bf16 hi+lo operands, fp32 accumulate in TMEM"}
+
+
 def _traffic(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
     current kernel source (null otherwise)."""
@@ -411,6 +456,8 @@ def main():
     ap.add_argument("--impl", default="ssoct", choices=["ssoct", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tc-axial", action="store_true", help="time the tensor-core axial form as the main line "
+                                                            "(profiling captures)")
     ap.add_argument("--size", default=None, help="NXxNYxNLAMBDA instead of the 1024x1024x256 workload "
                                                  "(profiling captures; not a bench line)")
     args = ap.parse_args()

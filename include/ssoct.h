@@ -62,6 +62,11 @@ typedef enum {
 
 /* Plan flags. */
 #define SSOCT_FLAG_MAGNITUDE 0x1u /* volume holds |V| instead of |V|^2 */
+/* Eq. 7 on the tensor cores: the sweep-axis DFT as two 16-point stages of
+ * tcgen05 MMAs with BF16 hi + lo operands and FP32 accumulation (relative L2
+ * error near 1e-5 instead of 1e-7).  nlambda = 256 only (else
+ * SSOCT_EUNSUPPORTED at plan creation). */
+#define SSOCT_FLAG_TC_AXIAL 0x2u
 
 /* Read-only facts about a plan. */
 typedef struct {

@@ -23,6 +23,7 @@ SSOCT_EDROPPED = 6
 SSOCT_ETIMEOUT = 7
 SSOCT_EUNSUPPORTED = 8
 SSOCT_FLAG_MAGNITUDE = 0x1
+SSOCT_FLAG_TC_AXIAL = 0x2
 
 STATUS_NAMES = {
     0: "SSOCT_OK", 1: "SSOCT_EINVAL", 2: "SSOCT_ENOMEM", 3: "SSOCT_ECUDA", 4: "SSOCT_EAGAIN",

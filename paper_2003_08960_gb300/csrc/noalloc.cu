@@ -93,8 +93,10 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
       {p.off_twx, p.twx.data(), sizeof(float2) * p.twx.size()},
       {p.off_twy, p.twy.data(), sizeof(float2) * p.twy.size()},
       {p.off_twl, p.twl.data(), sizeof(float2) * p.twl.size()},
+      {p.off_tcb, p.tcb.data(), sizeof(unsigned short) * p.tcb.size()},
   };
   for (const Up& u : ups) {
+    if (!u.n) continue;
     e = cudaMemcpyAsync(ws + u.off, u.src, u.n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
   }
@@ -141,7 +143,8 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
   ap.power_scale = (float)(p.alpha * p.alpha);
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
-  e = launch_axial(p, ap, s);
+  e = (p.flags & SSOCT_FLAG_TC_AXIAL) ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb), &lp.ctr->err, s)
+                                      : launch_axial(p, ap, s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("axial kernel launch: ") + cudaGetErrorString(e));
   return SSOCT_OK;
 }

@@ -40,7 +40,8 @@ struct Counters {
   // followed by rows_done[nlambda], cols_done[nlambda]
 };
 
-constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrTimeout = 1u;      // lateral kernel: a queue wait ran out
+constexpr unsigned kErrAxialTc = 2u;      // tensor-core axial kernel: an MMA wait ran out
 
 // Order in which the lateral kernel takes its items.  Step s holds the row
 // items of frame s (if s < nl) and then the column items of frame s - lag (if
@@ -148,6 +149,7 @@ struct Plan {
   // host tables
   std::vector<Tap> xtab, ytab;
   std::vector<float2> cx, cy, ox, oy, twx, twy, twl;
+  std::vector<unsigned short> tcb;  // SSOCT_FLAG_TC_AXIAL: BF16 hi / lo 16-point DFT matrix (operand layout)
   // geometry of the device work
   int n1x, n2x, n1y, n2y, n1l, n2l;
   int rows_per_item, cols_per_item;
@@ -156,7 +158,7 @@ struct Plan {
   LateralSchedule sch;
   // workspace layout (byte offsets)
   size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_ox, off_oy, off_twx, off_twy, off_twl;
-  size_t off_ring, off_scratch, off_inter, ws_bytes;
+  size_t off_tcb, off_ring, off_scratch, off_inter, ws_bytes;
   char* ws = nullptr;
   int device = -1;
   int num_sms = 0;
@@ -184,6 +186,14 @@ cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s);
 cudaError_t launch_cuts(const CutsParams& cp, cudaStream_t s);
 bool lateral_supported(int nx, int ny);
 bool axial_supported(int nl);
+// Tensor-core axial kernel (axial_tc.cu): sweep lengths it handles, its DFT
+// operand table, dynamic shared memory, and launcher.  err is the plan's error
+// word; the kernel ORs kErrAxialTc into it when an MMA wait runs out.
+bool axial_tc_supported(int nl);
+void axial_tc_table(std::vector<unsigned short>& out);
+size_t axial_tc_smem_bytes();
+cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigned short* bmat, unsigned* err,
+                            cudaStream_t s);
 // Dynamic shared memory of the lateral kernel for a plan (bytes).
 size_t lateral_smem_bytes(const Plan& p);
 // Columns per column item of the lateral kernel for a column length ny.

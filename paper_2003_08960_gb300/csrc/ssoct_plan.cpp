@@ -199,11 +199,12 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
     return SSOCT_EINVAL;
   for (int t = 0; t < nlambda; ++t)
     if (!(lambda_m[t] > 0.0) || !std::isfinite(lambda_m[t])) return SSOCT_EINVAL;
-  if (flags & ~SSOCT_FLAG_MAGNITUDE) return SSOCT_EINVAL;
+  if (flags & ~(SSOCT_FLAG_MAGNITUDE | SSOCT_FLAG_TC_AXIAL)) return SSOCT_EINVAL;
   ssoct_window w = win ? *win : ssoct_window{0, 0, nx, ny};
   if (w.x0 < 0 || w.y0 < 0 || w.wx < 1 || w.wy < 1 || w.x0 + w.wx > nx || w.y0 + w.wy > ny)
     return SSOCT_EINVAL;
   if (!lateral_supported(nx, ny) || !axial_supported(nlambda)) return SSOCT_EUNSUPPORTED;
+  if ((flags & SSOCT_FLAG_TC_AXIAL) && !axial_tc_supported(nlambda)) return SSOCT_EUNSUPPORTED;
 
   ssoct_plan h = new (std::nothrow) ssoct_plan_s();
   if (!h) return SSOCT_ENOMEM;
@@ -257,6 +258,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.twx = twiddles(nx, p.n1x, p.n2x, +1);
   p.twy = twiddles(ny, p.n1y, p.n2y, +1);
   p.twl = twiddles(nlambda, p.n1l, p.n2l, -1);
+  if (flags & SSOCT_FLAG_TC_AXIAL) axial_tc_table(p.tcb);
 
   // Work decomposition of the lateral kernel.
   p.rows_per_item = kThreads / p.n1x;
@@ -299,6 +301,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_twx = take(sizeof(float2) * p.twx.size());
   p.off_twy = take(sizeof(float2) * p.twy.size());
   p.off_twl = take(sizeof(float2) * p.twl.size());
+  p.off_tcb = take(sizeof(unsigned short) * p.tcb.size());
   p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
   p.off_scratch = take(sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
   p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
@@ -351,8 +354,10 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
       {p.off_twx, p.twx.data(), sizeof(float2) * p.twx.size()},
       {p.off_twy, p.twy.data(), sizeof(float2) * p.twy.size()},
       {p.off_twl, p.twl.data(), sizeof(float2) * p.twl.size()},
+      {p.off_tcb, p.tcb.data(), sizeof(unsigned short) * p.tcb.size()},
   };
   for (const Up& u : ups) {
+    if (!u.n) continue;
     e = cudaMemcpy(ws + u.off, u.src, u.n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(&p, e, "table upload");
   }
@@ -489,7 +494,10 @@ static ssoct_status launch_axial_pass(Plan& p, float* vol, void* cplx, cudaStrea
   ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
   ap.power_scale = (float)(p.alpha * p.alpha);
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
-  cudaError_t e = launch_axial(p, ap, s);
+  cudaError_t e = (p.flags & SSOCT_FLAG_TC_AXIAL)
+                      ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb),
+                                        &((Counters*)(ws + p.off_ctr))->err, s)
+                      : launch_axial(p, ap, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "axial kernel launch");
   if (ev) cudaEventRecord(ev[2], s);
   return SSOCT_OK;
@@ -592,7 +600,8 @@ ssoct_status ssoct_sync(ssoct_plan h, void* stream) {
   if (e != cudaSuccess) return cuda_fail(&p, e, "error word read");
   if (c.err) {
     cudaMemset(p.ws + p.off_ctr, 0, sizeof(Counters));
-    return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue");
+    if (c.err & kErrTimeout) return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue");
+    return fail(&p, SSOCT_ETIMEOUT, "tensor-core axial kernel gave up waiting on its MMAs");
   }
   return SSOCT_OK;
 }

@@ -62,6 +62,20 @@ def test_create_plan_validation(ss):
     assert st == ss.SSOCT_EUNSUPPORTED
     st, h = ss.ssoct_create_plan(64, 64, 24, 20e-6, 0.3, np.linspace(800e-9, 850e-9, 24))
     assert st == ss.SSOCT_EUNSUPPORTED
+    # unknown flag bits; the tensor-core axial form exists for nlambda = 256 only
+    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=0x4)
+    assert st == ss.SSOCT_EINVAL
+    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_TC_AXIAL)
+    assert st == ss.SSOCT_EUNSUPPORTED and h is None
+    lam256 = np.linspace(800e-9, 850e-9, 256)
+    st, h = ss.ssoct_create_plan(64, 64, 256, 20e-6, 0.3, lam256, flags=ss.SSOCT_FLAG_TC_AXIAL)
+    assert st == ss.SSOCT_OK
+    st, bytes_tc = ss.ssoct_workspace_size(h)
+    ss.ssoct_destroy_plan(h)
+    st, h = ss.ssoct_create_plan(64, 64, 256, 20e-6, 0.3, lam256)
+    st, bytes_plain = ss.ssoct_workspace_size(h)
+    ss.ssoct_destroy_plan(h)
+    assert bytes_tc - bytes_plain == 4096      # the BF16 hi / lo 32 x 32 operand table
 
 
 def test_plan_info_matches_closed_forms(ss):

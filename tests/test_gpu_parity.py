@@ -223,3 +223,68 @@ def test_sliding_gate_matches_oracle(ss):
     gate = stream[pushed - nl:pushed]
     ref = oracle.reconstruct(np.roll(gate, (pushed - nl) % nl, axis=0), a.pitch, a.z, a.lambdas)
     assert _rel(vol.cpu().numpy().astype(np.float64), oracle.intensity(ref)) <= 2 * TOL
+
+
+# Tensor-core axial form (SSOCT_FLAG_TC_AXIAL): BF16 hi + lo operands, FP32
+# accumulation.  Bound: relative L2 <= 1e-3 per volume against the FP64 oracle;
+# the split-precision arithmetic puts it near 1e-5, checked at 1e-4 as well.
+TC_TOL = 1e-3
+
+
+def _check_tc(vol, cplx, ref):
+    err_v = _rel(cplx.astype(np.complex128), ref)
+    err_p = _rel(vol.astype(np.float64), oracle.intensity(ref))
+    assert err_v <= TC_TOL and err_p <= 2 * TC_TOL, (err_v, err_p)
+    assert err_v <= 1e-4, f"tensor-core form rel L2 {err_v:.3e}, expected near 1e-5"
+    return err_v, err_p
+
+
+@pytest.mark.parametrize("shape,window", [((64, 64, 256), None), ((128, 64, 256), (20, 8, 77, 50)),
+                                          ((256, 256, 256), None)])
+def test_tc_axial_matches_oracle(ss, shape, window):
+    nx, ny, nl = shape
+    w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=nx + 3 * ny)
+    plan, vol, cplx, ref = _run(ss, w, window=window, method="fft", flags=ss.SSOCT_FLAG_TC_AXIAL)
+    err_v, err_p = _check_tc(vol, cplx, ref)
+    print(f"TC axial {shape} window={window}: complex rel L2 {err_v:.3e}, |V|^2 rel L2 {err_p:.3e}")
+
+
+def test_tc_axial_speckle_and_point_focus(ss):
+    """Speckle frames (fully developed, every bin populated) and the closed-form
+    focus of a point scatterer, both through the tensor-core form."""
+    w = synth.workload("custom", nx=128, ny=128, nlambda=256, kind="speckle", seed=5)
+    plan, vol, cplx, ref = _run(ss, w, method="fft", flags=ss.SSOCT_FLAG_TC_AXIAL)
+    _check_tc(vol, cplx, ref)
+    frames, lam, sc, dpx, dpy = pins.point_case(64, 256, 3.3, -5.2, 0.4e-3, ny=64)
+    plan = ss.Plan(64, 64, 256, pins.PITCH, pins.Z, lam, flags=ss.SSOCT_FLAG_TC_AXIAL)
+    vol = plan.reconstruct(_dev(frames)).cpu().numpy()
+    mask = np.zeros_like(vol, dtype=bool)
+    mask[:, 34:, 34:] = True
+    q, y, x = np.unravel_index(np.argmax(np.where(mask, vol, 0)), vol.shape)
+    ex, ey, eq = pins.expected_focus(64, 64, 256, lam, sc, dpx, dpy)
+    assert abs(x - ex) <= 1 and abs(y - ey) <= 1
+    dq = abs(q - eq) % 256
+    assert min(dq, 256 - dq) <= 1, (q, eq)
+
+
+def test_tc_axial_magnitude_and_sliding(ss):
+    w = synth.workload("custom", nx=64, ny=64, nlambda=256, kind="points", seed=9)
+    f = _dev(w.frames)
+    a = ss.Plan(w.nx, w.ny, 256, w.pitch, w.z, w.lambdas, flags=ss.SSOCT_FLAG_TC_AXIAL)
+    m = ss.Plan(w.nx, w.ny, 256, w.pitch, w.z, w.lambdas,
+                flags=ss.SSOCT_FLAG_TC_AXIAL | ss.SSOCT_FLAG_MAGNITUDE)
+    va, vm = a.reconstruct(f), m.reconstruct(f)
+    assert a.push(f) == ss.SSOCT_OK
+    vs = a.reconstruct_sliding()
+    a.sync()
+    m.sync()
+    assert torch.allclose(vm * vm, va, rtol=1e-5, atol=0)
+    assert torch.equal(vs, va)
+
+
+@pytest.mark.slow
+def test_tc_axial_paper_size_1024x1024x256(ss):
+    w = synth.workload("paper_1024x1024x256")
+    plan, vol, cplx, ref = _run(ss, w, method="fft", flags=ss.SSOCT_FLAG_TC_AXIAL)
+    err_v, err_p = _check_tc(vol, cplx, ref)
+    print(f"TC axial 1024x1024x256: complex rel L2 {err_v:.3e}, |V|^2 rel L2 {err_p:.3e}")
