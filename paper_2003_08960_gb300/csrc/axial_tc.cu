@@ -19,7 +19,10 @@
 // intermediate stores such a tile as 256 x 32 contiguous complex values): 4
 // blocks of 8 pixels, 24 MMAs per stage issued by one thread into 128 TMEM
 // columns, results read back with tcgen05.ld, |V|^2 staged in shared memory and
-// written as 128-byte rows of the volume.
+// written as 128-byte rows of the volume.  70 KB of shared memory, 128 TMEM
+// columns and at most 80 registers per thread let three CTAs share an SM, so
+// that one CTA's loads overlap the others' conversions and MMAs; one thread
+// waits for the MMAs while the rest wait at the CTA barrier.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -140,7 +143,7 @@ __device__ __forceinline__ void split2_bf16(float a, float b, unsigned& hi, unsi
 // i * 8 + pl keeps a warp's 32 pixels on distinct 16-byte slots of a core matrix.
 __device__ __forceinline__ int tc_row(int i, int pl) { return i * 8 + pl; }
 
-__global__ void __launch_bounds__(kTcThreads, 2) axial_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(kTcThreads, 3) axial_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // A operands: [hi / lo][block][128 x 32] BF16; the |V|^2 tile reuses them
   unsigned short* A = reinterpret_cast<unsigned short*>(smem);
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) axial_tc_kernel(const __grid_co
   float* out = reinterpret_cast<float*>(smem);               // [256][kOutStride] after stage 2
   __shared__ __align__(8) uint64_t bar;
   __shared__ unsigned tmem_base;
+  __shared__ int ok_flag;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int tile = blockIdx.x, kyw = blockIdx.y;
 
@@ -220,9 +224,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) axial_tc_kernel(const __grid_co
     }
     tc_commit(&bar);
   };
-  if (tid == 0) issue_stage();
-  const bool ok1 = __syncthreads_and(tc_wait(&bar, 0));
+  if (tid == 0) {
+    issue_stage();
+    ok_flag = tc_wait(&bar, 0) ? 1 : 0;
+  }
+  tc_fence_before();
+  __syncthreads();
   tc_fence_after();
+  const bool ok1 = ok_flag != 0;
 
   // 2. twiddle w256^(j1 k2) and re-layout as the stage-2 operand: row (pixel, k2),
   //    K = j1 (real) / 16 + j1 (imaginary).  Warp quadrant quad holds TMEM lanes
@@ -256,9 +265,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) axial_tc_kernel(const __grid_co
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid == 0 && ok1) issue_stage();
-  const bool ok2 = __syncthreads_and(ok1 && tc_wait(&bar, 1));
+  if (tid == 0) {
+    if (ok1) issue_stage();
+    ok_flag = (ok1 && tc_wait(&bar, 1)) ? 1 : 0;
+  }
+  tc_fence_before();
+  __syncthreads();
   tc_fence_after();
+  const bool ok2 = ok_flag != 0;
 
   // 3. V[k2 + 16 k1] sits in row (pixel, k2), columns k1 (real) / 16 + k1 (imaginary)
   const int kx0 = tile * kTile;
