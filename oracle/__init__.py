@@ -30,3 +30,4 @@ from .ssoct_oracle import (  # noqa: F401
     cuts,
     pixel_sample,
 )
+from . import aberration  # noqa: F401,E402  (Zernike pupil, sharpness and its gradient)
