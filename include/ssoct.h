@@ -67,6 +67,11 @@ typedef enum {
  * error near 1e-5 instead of 1e-7).  nlambda = 256 only (else
  * SSOCT_EUNSUPPORTED at plan creation). */
 #define SSOCT_FLAG_TC_AXIAL 0x2u
+/* Reserve the workspace of the aberration path (ssoct_set_pupil, ssoct_sharpness):
+ * the c P table, one complex frame per wavelength, partial sums.  Sizes: nx a
+ * power of two in 64..1024, ny in 64..512, nlambda in 16..512 (else
+ * SSOCT_EUNSUPPORTED at plan creation). */
+#define SSOCT_FLAG_PUPIL 0x4u
 
 /* Read-only facts about a plan. */
 typedef struct {
@@ -178,6 +183,29 @@ SSOCT_API ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan plan, const u
  * overwrites the intermediate, and the next sliding call redoes all nlambda
  * frames.  ENOTREADY before nlambda frames. */
 SSOCT_API ssoct_status ssoct_reconstruct_sliding(ssoct_plan plan, float* vol_dev, void* complex_dev, void* stream);
+
+/* Aberration correction (the paper names it as a use of the phase-resolved
+ * volume, introduction; it gives no method).  A phase screen
+ * exp(i sum_j c_j Z_j(rho, theta)) multiplies every rescaled frame together with
+ * the input chirp of Eq. 6; Z_j are the Noll-ordered Zernike polynomials
+ * j = 1..15 (Noll 1976), RMS-normalised on the unit disk, with rho the sensor
+ * radius (pixel centre N/2) over min(nx, ny) d / 2, continued outside the disk.
+ * Sets the coefficients (radians; coeffs[j - 1] = c_j, ncoeffs 0..15, missing
+ * ones 0) and the distance z_m used by ssoct_sharpness (the plan's own z stays
+ * in use for the other calls).  Needs SSOCT_FLAG_PUPIL and a workspace; blocks
+ * until the table is in device memory. */
+SSOCT_API ssoct_status ssoct_set_pupil(ssoct_plan plan, const double* coeffs, int ncoeffs, double z_m);
+
+/* Sharpness of the pupil-corrected volume and its gradient, by one forward and
+ * one hand-written adjoint pass (all on the device; FP64 sums).  With
+ * P_v = |V_v|^2 of Eq. 7 over the window, L = - sum_v P_v^2 / (sum_v P_v)^2.
+ * vol_dev [nlambda][wy][wx] (16-byte aligned) receives P.  out_host[17]
+ * receives L, dL/dz (per metre, at the z of ssoct_set_pupil) and
+ * dL/dc_1 .. dL/dc_15.  Uses the plan's sweep-axis intermediate (like the
+ * reconstruct calls, it invalidates the sliding-gate state).  Synchronises
+ * `stream`.  ENOTREADY before ssoct_set_pupil. */
+SSOCT_API ssoct_status ssoct_sharpness(ssoct_plan plan, const uint16_t* frames_dev, float* vol_dev,
+                                       double* out_host, void* stream);
 
 /* The three orthogonal cuts of a volume written by a reconstruct call with this
  * plan (text after Eq. 7; Fig. 5): xy[wy][wx] = P(x, y, z0), xz[nlambda][wx] =

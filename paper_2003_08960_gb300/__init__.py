@@ -21,7 +21,7 @@ import numpy as np
 from . import _abi
 from ._abi import (  # noqa: F401
     SSOCT_EDROPPED, SSOCT_EINVAL, SSOCT_ENOMEM, SSOCT_ENOTREADY, SSOCT_EUNSUPPORTED, SSOCT_ETIMEOUT,
-    SSOCT_FLAG_MAGNITUDE, SSOCT_FLAG_TC_AXIAL, SSOCT_OK, ssoct_plan_info_t, ssoct_window,
+    SSOCT_FLAG_MAGNITUDE, SSOCT_FLAG_PUPIL, SSOCT_FLAG_TC_AXIAL, SSOCT_OK, ssoct_plan_info_t, ssoct_window,
 )
 
 
@@ -106,6 +106,19 @@ def ssoct_get_cuts(plan, vol_ptr: int, x0: int, y0: int, z0: int, xy_ptr: int, x
 
 def ssoct_sync(plan, stream: int) -> int:
     return _abi.lib().ssoct_sync(plan, C.c_void_p(stream))
+
+
+def ssoct_set_pupil(plan, coeffs: Sequence[float], z_m: float) -> int:
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    return _abi.lib().ssoct_set_pupil(plan, c.ctypes.data_as(C.POINTER(C.c_double)), int(c.size), float(z_m))
+
+
+def ssoct_sharpness(plan, frames_ptr: int, vol_ptr: int, stream: int):
+    """Returns (status, out[17]): loss, dL/dz, dL/dc_1 .. dL/dc_15."""
+    out = np.zeros(17, dtype=np.float64)
+    st = _abi.lib().ssoct_sharpness(plan, C.c_void_p(frames_ptr), C.c_void_p(vol_ptr),
+                                    out.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(stream))
+    return st, out
 
 
 def ssoct_inject_stall(plan, skip: int, wait_limit_ns: int) -> int:
@@ -254,3 +267,12 @@ class Plan:
 
     def sync(self, stream=None) -> None:
         _check(ssoct_sync(self._h, _stream_ptr(stream)), self._h, "sync")
+
+    def sharpness(self, frames, coeffs: Sequence[float], z_m: float, out=None, stream=None):
+        """(loss, grad[16], volume) of the pupil-corrected reconstruction: grad[0] =
+        dL/dz, grad[j] = dL/dc_j (needs a plan made with SSOCT_FLAG_PUPIL)."""
+        _check(ssoct_set_pupil(self._h, coeffs, z_m), self._h, "set_pupil")
+        vol = out if out is not None else self.empty_volume()[0]
+        st, res = ssoct_sharpness(self._h, frames.data_ptr(), vol.data_ptr(), _stream_ptr(stream))
+        _check(st, self._h, "sharpness")
+        return float(res[0]), res[1:].copy(), vol

@@ -24,6 +24,7 @@ SSOCT_ETIMEOUT = 7
 SSOCT_EUNSUPPORTED = 8
 SSOCT_FLAG_MAGNITUDE = 0x1
 SSOCT_FLAG_TC_AXIAL = 0x2
+SSOCT_FLAG_PUPIL = 0x4
 
 STATUS_NAMES = {
     0: "SSOCT_OK", 1: "SSOCT_EINVAL", 2: "SSOCT_ENOMEM", 3: "SSOCT_ECUDA", 4: "SSOCT_EAGAIN",
@@ -67,6 +68,8 @@ SIGNATURES = {
     "ssoct_get_cuts": (C.c_int, [ssoct_plan, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssoct_sync": (C.c_int, [ssoct_plan, C.c_void_p]),
+    "ssoct_set_pupil": (C.c_int, [ssoct_plan, C.POINTER(C.c_double), C.c_int, C.c_double]),
+    "ssoct_sharpness": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "ssoct_inject_stall": (C.c_int, [ssoct_plan, C.c_uint, C.c_ulonglong]),
     "ssoct_profile": (C.c_int, [ssoct_plan, C.c_int]),
     "ssoct_profile_read": (C.c_int, [ssoct_plan, C.POINTER(C.c_double), C.POINTER(C.c_double),

@@ -150,6 +150,11 @@ struct Plan {
   std::vector<Tap> xtab, ytab;
   std::vector<float2> cx, cy, ox, oy, twx, twy, twl;
   std::vector<unsigned short> tcb;  // SSOCT_FLAG_TC_AXIAL: BF16 hi / lo 16-point DFT matrix (operand layout)
+  // SSOCT_FLAG_PUPIL: input chirp x Zernike screen, its distance z and |K|, frames per Q chunk
+  std::vector<float2> cp;
+  double sh_z = 0.0, sh_alpha = 0.0;
+  int sh_tpc = 8;
+  bool sh_ready = false;
   // geometry of the device work
   int n1x, n2x, n1y, n2y, n1l, n2l;
   int rows_per_item, cols_per_item;
@@ -159,6 +164,7 @@ struct Plan {
   // workspace layout (byte offsets)
   size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_ox, off_oy, off_twx, off_twy, off_twl;
   size_t off_tcb, off_ring, off_scratch, off_inter, ws_bytes;
+  size_t off_cp = 0, off_F = 0, off_Q = 0, off_red = 0;  // SSOCT_FLAG_PUPIL regions
   char* ws = nullptr;
   int device = -1;
   int num_sms = 0;
@@ -194,6 +200,13 @@ void axial_tc_table(std::vector<unsigned short>& out);
 size_t axial_tc_smem_bytes();
 cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigned short* bmat, unsigned* err,
                             cudaStream_t s);
+// Aberration path (sharpness.cu): sizes it compiles, the c P table, and the
+// forward + adjoint launches that leave loss and gradient in the FP64 block at
+// off_red ([0] S1, [1] S2, [2] loss, [3] dL/dz, [4..18] dL/dc_1..15).
+constexpr int kShRedDoubles = 19;
+bool sharpness_supported(int nx, int ny, int nl);
+void build_pupil_table(int nx, int ny, double alpha, const double* coeffs, int ncoeffs, std::vector<float2>& out);
+cudaError_t launch_sharpness(const Plan& pl, const uint16_t* frames, float* vol, cudaStream_t s);
 // Dynamic shared memory of the lateral kernel for a plan (bytes).
 size_t lateral_smem_bytes(const Plan& p);
 // Columns per column item of the lateral kernel for a column length ny.

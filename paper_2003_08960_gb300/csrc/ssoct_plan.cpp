@@ -199,12 +199,13 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
     return SSOCT_EINVAL;
   for (int t = 0; t < nlambda; ++t)
     if (!(lambda_m[t] > 0.0) || !std::isfinite(lambda_m[t])) return SSOCT_EINVAL;
-  if (flags & ~(SSOCT_FLAG_MAGNITUDE | SSOCT_FLAG_TC_AXIAL)) return SSOCT_EINVAL;
+  if (flags & ~(SSOCT_FLAG_MAGNITUDE | SSOCT_FLAG_TC_AXIAL | SSOCT_FLAG_PUPIL)) return SSOCT_EINVAL;
   ssoct_window w = win ? *win : ssoct_window{0, 0, nx, ny};
   if (w.x0 < 0 || w.y0 < 0 || w.wx < 1 || w.wy < 1 || w.x0 + w.wx > nx || w.y0 + w.wy > ny)
     return SSOCT_EINVAL;
   if (!lateral_supported(nx, ny) || !axial_supported(nlambda)) return SSOCT_EUNSUPPORTED;
   if ((flags & SSOCT_FLAG_TC_AXIAL) && !axial_tc_supported(nlambda)) return SSOCT_EUNSUPPORTED;
+  if ((flags & SSOCT_FLAG_PUPIL) && !sharpness_supported(nx, ny, nlambda)) return SSOCT_EUNSUPPORTED;
 
   ssoct_plan h = new (std::nothrow) ssoct_plan_s();
   if (!h) return SSOCT_ENOMEM;
@@ -305,6 +306,13 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
   p.off_scratch = take(sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
   p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
+  if (flags & SSOCT_FLAG_PUPIL) {
+    const size_t chunks = (size_t)(nlambda + p.sh_tpc - 1) / p.sh_tpc;
+    p.off_cp = take(sizeof(float2) * (size_t)nx * ny);
+    p.off_F = take(sizeof(float2) * (size_t)nlambda * ny * nx);
+    p.off_Q = take(sizeof(float2) * chunks * ny * nx);
+    p.off_red = take(sizeof(double) * kShRedDoubles);
+  }
   p.ws_bytes = off;
   *out = h;
   return SSOCT_OK;
@@ -603,6 +611,43 @@ ssoct_status ssoct_sync(ssoct_plan h, void* stream) {
     if (c.err & kErrTimeout) return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue");
     return fail(&p, SSOCT_ETIMEOUT, "tensor-core axial kernel gave up waiting on its MMAs");
   }
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_set_pupil(ssoct_plan h, const double* coeffs, int ncoeffs, double z_m) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!(p.flags & SSOCT_FLAG_PUPIL)) return fail(&p, SSOCT_EINVAL, "plan created without SSOCT_FLAG_PUPIL");
+  if (ncoeffs < 0 || ncoeffs > 15 || (ncoeffs > 0 && !coeffs)) return fail(&p, SSOCT_EINVAL, "need 0..15 coefficients");
+  if (z_m == 0.0 || !std::isfinite(z_m)) return fail(&p, SSOCT_EINVAL, "z must be finite and non-zero");
+  for (int j = 0; j < ncoeffs; ++j)
+    if (!std::isfinite(coeffs[j])) return fail(&p, SSOCT_EINVAL, "coefficients must be finite");
+  if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
+  p.sh_z = z_m;
+  p.sh_alpha = p.pitch * p.pitch / (p.lambda1 * z_m);
+  build_pupil_table(p.nx, p.ny, p.sh_alpha, coeffs, ncoeffs, p.cp);
+  cudaError_t e = cudaMemcpy(p.ws + p.off_cp, p.cp.data(), sizeof(float2) * p.cp.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "pupil table upload");
+  p.sh_ready = true;
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_sharpness(ssoct_plan h, const uint16_t* frames_dev, float* vol_dev, double* out_host, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!(p.flags & SSOCT_FLAG_PUPIL)) return fail(&p, SSOCT_EINVAL, "plan created without SSOCT_FLAG_PUPIL");
+  if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
+  if (!p.sh_ready) return fail(&p, SSOCT_ENOTREADY, "ssoct_set_pupil has not been called");
+  if (!frames_dev || !vol_dev || !out_host || ((uintptr_t)vol_dev % 16))
+    return fail(&p, SSOCT_EINVAL, "frames, volume (16-byte aligned) and output must be non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  p.lat_upto = -1;  // the intermediate no longer holds sliding-gate holograms
+  cudaError_t e = launch_sharpness(p, frames_dev, vol_dev, s);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "sharpness kernels");
+  e = cudaMemcpyAsync(out_host, p.ws + p.off_red + 2 * sizeof(double), 17 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "loss and gradient read-back");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "stream synchronize");
   return SSOCT_OK;
 }
 

@@ -63,7 +63,7 @@ def test_create_plan_validation(ss):
     st, h = ss.ssoct_create_plan(64, 64, 24, 20e-6, 0.3, np.linspace(800e-9, 850e-9, 24))
     assert st == ss.SSOCT_EUNSUPPORTED
     # unknown flag bits; the tensor-core axial form exists for nlambda = 256 only
-    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=0x4)
+    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=0x8)
     assert st == ss.SSOCT_EINVAL
     st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_TC_AXIAL)
     assert st == ss.SSOCT_EUNSUPPORTED and h is None
@@ -76,6 +76,31 @@ def test_create_plan_validation(ss):
     st, bytes_plain = ss.ssoct_workspace_size(h)
     ss.ssoct_destroy_plan(h)
     assert bytes_tc - bytes_plain == 4096      # the BF16 hi / lo 32 x 32 operand table
+
+
+def test_pupil_plan_validation(ss):
+    """The aberration path: sizes it compiles, its workspace, and the calls it
+    refuses without the flag, without a workspace or with bad coefficients."""
+    st, h = ss.ssoct_create_plan(96, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_PUPIL)
+    assert st == ss.SSOCT_EUNSUPPORTED
+    st, h = ss.ssoct_create_plan(64, 1024, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_PUPIL)
+    assert st == ss.SSOCT_EUNSUPPORTED
+    st, plain = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM)
+    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_PUPIL)
+    assert st == ss.SSOCT_OK
+    _, b0 = ss.ssoct_workspace_size(plain)
+    _, b1 = ss.ssoct_workspace_size(h)
+    # c P table + one complex frame per wavelength + 4 chunks of partial Q + FP64 block, each 256-aligned
+    assert b1 - b0 == 64 * 64 * 8 + 32 * 64 * 64 * 8 + 4 * 64 * 64 * 8 + 256
+    assert ss.ssoct_set_pupil(plain, [0.1] * 15, 0.3) == ss.SSOCT_EINVAL
+    assert ss.ssoct_set_pupil(h, [0.1] * 16, 0.3) == ss.SSOCT_EINVAL
+    assert ss.ssoct_set_pupil(h, [float("nan")], 0.3) == ss.SSOCT_EINVAL
+    assert ss.ssoct_set_pupil(h, [0.1] * 15, 0.0) == ss.SSOCT_EINVAL
+    assert ss.ssoct_set_pupil(h, [0.1] * 15, 0.3) == ss.SSOCT_ENOMEM      # no workspace yet
+    st, out = ss.ssoct_sharpness(h, 0, 0, 0)
+    assert st == ss.SSOCT_ENOMEM
+    ss.ssoct_destroy_plan(plain)
+    ss.ssoct_destroy_plan(h)
 
 
 def test_plan_info_matches_closed_forms(ss):
