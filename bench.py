@@ -241,6 +241,7 @@ def run_ssoct(args):
     peak, peak_kind = _peaks()
     tc = None if (args.tc_axial or args.no_e2e) else _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak)
     sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if not args.no_e2e else None
+    aberration = _aberration(args, ss, torch, synth, stream) if not args.no_e2e else None
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
     e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
@@ -275,6 +276,7 @@ def run_ssoct(args):
         "e2e": e2e,
         "sliding": sliding,
         "tc_axial": tc,
+        "aberration": aberration,
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
@@ -431,6 +433,31 @@ def _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak):
             "axial_frac": ax_bytes / (ax_ms * 1e-3) / 1e9 / peak,
             "rel_l2_vs_fp32_volume": float(d),
             "form": "axial DFT as two 16-point tcgen05 MMA stages, bf16 hi+lo operands, fp32 accumulate in TMEM"}
+
+
+def _aberration(args, ss, torch, synth, stream, steps=10):
+    """Sharpness loss + gradient (dL/dz, dL/dc_1..15) per call of ssoct_sharpness on
+    the 512x512x128 speckle sweep with 15 Zernike coefficients ~ N(0, 0.5 rad),
+    reconstructed 5 mm beyond the generating distance.  Each call runs the forward
+    and adjoint kernels and reads the 17 results back (it synchronises)."""
+    import time
+    w = synth.workload("mid_512x512x128")
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=ss.SSOCT_FLAG_PUPIL)
+    frames = torch.from_numpy(w.frames.view(np.int16)).cuda()
+    vol, _ = plan.empty_volume()
+    coeffs = np.random.default_rng(5).normal(0.0, 0.5, 15)
+    for _ in range(max(args.warmup, 3)):
+        loss, grad, _ = plan.sharpness(frames, coeffs, w.z + 5e-3, out=vol, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        loss, grad, _ = plan.sharpness(frames, coeffs, w.z + 5e-3, out=vol, stream=stream)
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    voxels = w.nx * w.ny * w.nlambda
+    return {"workload": f"{w.nx}x{w.ny}x{w.nlambda} speckle, 15 Zernike coefficients, z + 5 mm",
+            "ms_per_gradient": ms, "Gvoxel_per_s": voxels / (ms * 1e-3) / 1e9, "loss": loss,
+            "grad_norm": float(np.linalg.norm(grad)),
+            "note": "host wall time per ssoct_sharpness call (forward + adjoint + 17 doubles read back)"}
 
 
 def _traffic(kernel: str):

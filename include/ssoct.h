@@ -89,10 +89,15 @@ typedef struct {
 } ssoct_plan_info_t;
 
 /* Create a plan.  Host only: no CUDA call is made here.
- *   nx, ny     frame size (pixels).  This build compiles nx, ny in {64, 128,
- *              256, 512, 1024} (square), plus (128, 64) and (64, 128).
+ *   nx, ny     frame size (pixels).  The persistent lateral kernel compiles
+ *              nx, ny in {64, 128, 256, 512, 1024} (square), plus (128, 64) and
+ *              (64, 128).  Any other pair from {64, 128, 256, 384, 512, 640,
+ *              768, 1024} (mixed radix 2/3/5) takes a two-pass lateral path
+ *              (row pass, column pass through a frame buffer in the
+ *              workspace); such plans do not offer ssoct_reconstruct_sliding
+ *              or ssoct_reconstruct_frames_noalloc (EUNSUPPORTED there).
  *   nlambda    frames per sweep = depth bins, N_z of Eq. 3 / the gate of Eq. 7.
- *              This build compiles {16, 32, 64, 128, 256, 512}.
+ *              This build compiles {16, 32, 64, 96, 128, 160, 200, 256, 512}.
  *   pitch_m    camera pixel pitch d > 0.
  *   z_m        sensor-to-object distance z != 0 of Eq. 6.
  *   lambda_m   [nlambda] wavelength of each frame of the sweep, > 0; copied.

@@ -17,6 +17,7 @@ namespace {
 template <int NL>
 __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_kernel(const __grid_constant__ AxialParams p) {
   constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  static_assert(N2 % N1 == 0, "the second stage needs N1 | N2");
   extern __shared__ __align__(16) unsigned char smem[];
   float2* ex = reinterpret_cast<float2*>(smem);
   const int tile = blockIdx.x;
@@ -71,7 +72,7 @@ cudaError_t launch(const AxialParams& ap, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-#define SSOCT_AXIAL_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512)
+#define SSOCT_AXIAL_SIZES(X) X(16) X(32) X(64) X(96) X(128) X(160) X(200) X(256) X(512)
 
 }  // namespace
 

@@ -16,7 +16,7 @@ template <int N>
 struct Split {
   static constexpr int N1 = split_n1(N);
   static constexpr int N2 = N1 ? N / N1 : 0;
-  static_assert(N1 > 0 && N2 % N1 == 0, "FFT length not built");
+  static_assert(N1 > 0 && N1 * N2 == N, "FFT length not built");
 };
 
 // f(integral_constant<int, I>) for I = B .. E-1, unrolled at compile time.

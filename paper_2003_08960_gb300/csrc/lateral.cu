@@ -558,6 +558,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap,
                    const __grid_constant__ CUtensorMap tmap_inter) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
+  static_assert(Split<NX>::N2 % Split<NX>::N1 == 0 && Split<NY>::N2 % Split<NY>::N1 == 0,
+                "the second stage needs N1 | N2");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t done_bar[kStages];

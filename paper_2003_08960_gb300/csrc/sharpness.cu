@@ -29,6 +29,19 @@ namespace {
 constexpr int kRowThreads = 256;
 constexpr int kGradThreads = 256;
 
+// Split N = N1 x N2 of one axis for these kernels: stage 1 is N2-point DFTs in
+// the N1 threads of a transform, stage 2 the N2 N1-point DFTs spread over those
+// threads, NI per thread (the last ones idle when N1 does not divide N2, e.g.
+// 640 = 32 x 20).  AS is the register array length, TW the width of a column
+// tile (16 when 32 N1 threads would exceed 512).
+template <int N>
+struct Lat {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int NI = (N2 + N1 - 1) / N1;
+  static constexpr int AS = NI * N1 > N2 ? NI * N1 : N2;
+  static constexpr int TW = kTile * N1 <= 512 ? kTile : kTile / 2;
+};
+
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
 __device__ __forceinline__ float u16_to_float(const uint16_t* p) { return (float)__ldg(p); }
@@ -42,13 +55,13 @@ __device__ __forceinline__ float resample(const uint16_t* fr, int nx, const Tap&
   return fmaf(ty.w0, v0, ty.w1 * v1);
 }
 
-// Row DFT of sign S over the registers a[N2] of thread (r, j1) of an N1 x N2
-// split: on entry a[j2] = x[j1 + N1 j2]; on exit a[i N1 + k1] = X[k2 + N2 k1]
-// with k2 = j1 + N1 i.  ex is this row's padded exchange block; a row's N1
-// threads lie in one warp.
+// Row DFT of sign S over the registers of thread (r, j1) of an N1 x N2 split:
+// on entry a[j2] = x[j1 + N1 j2]; on exit a[i N1 + k1] = X[k2 + N2 k1] with
+// k2 = j1 + N1 i for the i with k2 < N2.  ex is this row's padded exchange
+// block; a row's N1 threads lie in one warp.
 template <int N, int S>
-__device__ __forceinline__ void row_dft(float2 (&a)[Split<N>::N2], const float2* tw, float2* ex, int j1) {
-  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+__device__ __forceinline__ void row_dft(float2 (&a)[Lat<N>::AS], const float2* tw, float2* ex, int j1) {
+  constexpr int N1 = Lat<N>::N1, N2 = Lat<N>::N2, NI = Lat<N>::NI;
   Dft<N2, S>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) {
@@ -59,21 +72,23 @@ __device__ __forceinline__ void row_dft(float2 (&a)[Split<N>::N2], const float2*
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) ex[k2 * (N1 + 1) + j1] = a[k2];
   __syncwarp();
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
-    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[k2 * (N1 + 1) + jj];
-    Dft<N1, S>::template run<1, i * N1>(a);
+      for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[k2 * (N1 + 1) + jj];
+      Dft<N1, S>::template run<1, i * N1>(a);
+    }
   });
 }
 
 // Column DFT of sign S over 32-wide tiles: thread (pix, j1), a[j2] = x[j1 + N1 j2]
 // on entry, a[i N1 + k1] = X[k2 + N2 k1] (k2 = j1 + N1 i) on exit.  tw holds the
 // twiddles of sign TS (conjugated when S differs).
-template <int N, int S, int TS>
-__device__ __forceinline__ void col_dft(float2 (&a)[Split<N>::N2], const float2* tw, float2* ex, int j1, int pix) {
-  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+template <int N, int S, int TS, int TW>
+__device__ __forceinline__ void col_dft(float2 (&a)[Lat<N>::AS], const float2* tw, float2* ex, int j1, int pix) {
+  constexpr int N1 = Lat<N>::N1, N2 = Lat<N>::N2, NI = Lat<N>::NI;
   Dft<N2, S>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) {
@@ -82,14 +97,16 @@ __device__ __forceinline__ void col_dft(float2 (&a)[Split<N>::N2], const float2*
   }
   __syncthreads();
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * kTile + pix] = a[k2];
+  for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * TW + pix] = a[k2];
   __syncthreads();
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
-    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * kTile + pix];
-    Dft<N1, S>::template run<1, i * N1>(a);
+      for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * TW + pix];
+      Dft<N1, S>::template run<1, i * N1>(a);
+    }
   });
 }
 
@@ -107,6 +124,7 @@ struct ShParams {
   const float* vol;        // [nl][wy][wx] P_v
   double* red;             // [0] S1, [1] S2, [2..18] loss, dL/dz, dL/dc_1..15
   int nx, ny, nl, x0, y0, wx, wy, ntx, tpc;
+  int ring_start;          // frame t of the gate is frames[(ring_start + t) mod nl]
   float alpha2;            // |K|^2
   double scale_z;          // pi |K| / z
 };
@@ -115,15 +133,15 @@ struct ShParams {
 
 template <int NX>
 __global__ void __launch_bounds__(kRowThreads) rows_fwd_kernel(const __grid_constant__ ShParams p) {
-  constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2, RPI = kRowThreads / N1;
+  constexpr int N1 = Lat<NX>::N1, N2 = Lat<NX>::N2, RPI = kRowThreads / N1;
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = threadIdx.x / N1, j1 = threadIdx.x % N1;
   const int y = blockIdx.x * RPI + r, t = blockIdx.y;
   float2* ex = reinterpret_cast<float2*>(smem) + r * N2 * (N1 + 1);
-  const uint16_t* fr = p.frames + (size_t)t * p.ny * NX;
+  const uint16_t* fr = p.frames + (size_t)((p.ring_start + t) % p.nl) * p.ny * NX;
   const Tap ty = p.ytab[(size_t)t * p.ny + y];
   const float2* cp = p.cp + (size_t)y * NX;
-  float2 a[N2];
+  float2 a[Lat<NX>::AS];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) {
     const int n = j1 + N1 * j2;
@@ -133,36 +151,40 @@ __global__ void __launch_bounds__(kRowThreads) rows_fwd_kernel(const __grid_cons
   }
   row_dft<NX, 1>(a, p.twx, ex, j1);
   float2* dst = p.F + ((size_t)t * p.ny + y) * NX;
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, Lat<NX>::NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) dst[k2 + N2 * k1] = a[i * N1 + k1];
+      for (int k1 = 0; k1 < N1; ++k1) dst[k2 + N2 * k1] = a[i * N1 + k1];
+    }
   });
 }
 
 template <int NY>
-__global__ void __launch_bounds__(kTile * Split<NY>::N1) cols_fwd_kernel(const __grid_constant__ ShParams p) {
-  constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
+__global__ void __launch_bounds__(Lat<NY>::TW * Lat<NY>::N1) cols_fwd_kernel(const __grid_constant__ ShParams p) {
+  constexpr int N1 = Lat<NY>::N1, N2 = Lat<NY>::N2, TW = Lat<NY>::TW;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int pix = threadIdx.x % kTile, j1 = threadIdx.x / kTile;
-  const int x = blockIdx.x * kTile + pix, t = blockIdx.y;
+  const int pix = threadIdx.x % TW, j1 = threadIdx.x / TW;
+  const int x = blockIdx.x * TW + pix, t = blockIdx.y;
   const float2* src = p.F + (size_t)t * NY * p.nx + x;
-  float2 a[N2];
+  float2 a[Lat<NY>::AS];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = src[(size_t)(j1 + N1 * j2) * p.nx];
-  col_dft<NY, 1, 1>(a, p.twy, reinterpret_cast<float2*>(smem), j1, pix);
+  col_dft<NY, 1, 1, TW>(a, p.twy, reinterpret_cast<float2*>(smem), j1, pix);
   const int kxw = x - p.x0;
   if (kxw < 0 || kxw >= p.wx) return;
   float2* dst = p.inter + ((size_t)(kxw / kTile) * p.nl + t) * kTile + kxw % kTile;
   const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, Lat<NY>::NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      const int kyw = k2 + N2 * k1 - p.y0;
-      if (kyw >= 0 && kyw < p.wy) dst[(size_t)kyw * row_pitch] = a[i * N1 + k1];
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int kyw = k2 + N2 * k1 - p.y0;
+        if (kyw >= 0 && kyw < p.wy) dst[(size_t)kyw * row_pitch] = a[i * N1 + k1];
+      }
     }
   });
 }
@@ -201,6 +223,7 @@ __global__ void __launch_bounds__(kGradThreads) sums_kernel(const __grid_constan
 template <int NL>
 __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_adj_kernel(const __grid_constant__ ShParams p) {
   constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  static_assert(N2 % N1 == 0, "sweep lengths split with N1 | N2");
   extern __shared__ __align__(16) unsigned char smem[];
   float2* ex = reinterpret_cast<float2*>(smem);
   const int pix = threadIdx.x % kTile, j1 = threadIdx.x / kTile;
@@ -210,7 +233,7 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_adj_kernel(const 
   float2 a[N2];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = g[(j1 + N1 * j2) * kTile];
-  col_dft<NL, -1, -1>(a, p.twl, ex, j1, pix);  // V~[q = k2 + N2 k1]
+  col_dft<NL, -1, -1, kTile>(a, p.twl, ex, j1, pix);  // V~[q = k2 + N2 k1]
   __syncthreads();
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -227,7 +250,7 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_adj_kernel(const 
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = ex[(j1 + N1 * j2) * kTile + pix];
   // sum_q W_q exp(+2 pi i q t / NL): the same split with the conjugate twiddles
-  col_dft<NL, 1, -1>(a, p.twl, ex, j1, pix);
+  col_dft<NL, 1, -1, kTile>(a, p.twl, ex, j1, pix);
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
@@ -237,70 +260,76 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_adj_kernel(const 
 }
 
 template <int NY>
-__global__ void __launch_bounds__(kTile * Split<NY>::N1) cols_adj_kernel(const __grid_constant__ ShParams p) {
-  constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
+__global__ void __launch_bounds__(Lat<NY>::TW * Lat<NY>::N1) cols_adj_kernel(const __grid_constant__ ShParams p) {
+  constexpr int N1 = Lat<NY>::N1, N2 = Lat<NY>::N2, TW = Lat<NY>::TW;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int pix = threadIdx.x % kTile, j1 = threadIdx.x / kTile;
-  const int x = blockIdx.x * kTile + pix, t = blockIdx.y;
+  const int pix = threadIdx.x % TW, j1 = threadIdx.x / TW;
+  const int x = blockIdx.x * TW + pix, t = blockIdx.y;
   const int kxw = x - p.x0;
   const bool inx = kxw >= 0 && kxw < p.wx;
   const float2* src = p.inter + ((size_t)(inx ? kxw / kTile : 0) * p.nl + t) * kTile + (inx ? kxw % kTile : 0);
   const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
-  float2 a[N2];
+  float2 a[Lat<NY>::AS];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) {
     const int kyw = j1 + N1 * j2 - p.y0;
     a[j2] = (inx && kyw >= 0 && kyw < p.wy) ? src[(size_t)kyw * row_pitch] : make_float2(0.f, 0.f);
   }
   // the adjoint of the forward column DFT (+) is the column DFT (-), with the forward table conjugated
-  col_dft<NY, -1, 1>(a, p.twy, reinterpret_cast<float2*>(smem), j1, pix);
+  col_dft<NY, -1, 1, TW>(a, p.twy, reinterpret_cast<float2*>(smem), j1, pix);
   float2* dst = p.F + (size_t)t * NY * p.nx + x;
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, Lat<NY>::NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)(k2 + N2 * k1) * p.nx] = a[i * N1 + k1];
+      for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)(k2 + N2 * k1) * p.nx] = a[i * N1 + k1];
+    }
   });
 }
 
 template <int NX>
 __global__ void __launch_bounds__(kRowThreads) rows_adj_kernel(const __grid_constant__ ShParams p) {
-  constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2, RPI = kRowThreads / N1;
+  constexpr int N1 = Lat<NX>::N1, N2 = Lat<NX>::N2, RPI = kRowThreads / N1, AS = Lat<NX>::AS;
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = threadIdx.x / N1, j1 = threadIdx.x % N1;
   const int y = blockIdx.x * RPI + r, chunk = blockIdx.y;
   float2* ex = reinterpret_cast<float2*>(smem) + r * N2 * (N1 + 1);
   const int t0 = chunk * p.tpc, t1 = min(p.nl, t0 + p.tpc);
-  float2 acc[N2];
+  float2 acc[AS];
 #pragma unroll
-  for (int i = 0; i < N2; ++i) acc[i] = make_float2(0.f, 0.f);
+  for (int i = 0; i < AS; ++i) acc[i] = make_float2(0.f, 0.f);
   for (int t = t0; t < t1; ++t) {
     const float2* src = p.F + ((size_t)t * p.ny + y) * NX;
-    float2 a[N2];
+    float2 a[AS];
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) a[j2] = src[j1 + N1 * j2];
     row_dft<NX, -1>(a, p.twx, ex, j1);
-    const uint16_t* fr = p.frames + (size_t)t * p.ny * NX;
+    const uint16_t* fr = p.frames + (size_t)((p.ring_start + t) % p.nl) * p.ny * NX;
     const Tap ty = p.ytab[(size_t)t * p.ny + y];
     const Tap* xt = p.xtab + (size_t)t * NX;
-    static_for<0, N2 / N1>([&](auto I) {
+    static_for<0, Lat<NX>::NI>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const int k2 = j1 + N1 * i;
+      if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const float u = resample(fr, NX, xt[k2 + N2 * k1], ty);
-        const float2 v = a[i * N1 + k1];
-        acc[i * N1 + k1].x = fmaf(v.x, u, acc[i * N1 + k1].x);   // conj(Y) u
-        acc[i * N1 + k1].y = fmaf(-v.y, u, acc[i * N1 + k1].y);
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const float u = resample(fr, NX, xt[k2 + N2 * k1], ty);
+          const float2 v = a[i * N1 + k1];
+          acc[i * N1 + k1].x = fmaf(v.x, u, acc[i * N1 + k1].x);   // conj(Y) u
+          acc[i * N1 + k1].y = fmaf(-v.y, u, acc[i * N1 + k1].y);
+        }
       }
     });
   }
   float2* dst = p.qpart + ((size_t)chunk * p.ny + y) * NX;
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, Lat<NX>::NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) dst[k2 + N2 * k1] = acc[i * N1 + k1];
+      for (int k1 = 0; k1 < N1; ++k1) dst[k2 + N2 * k1] = acc[i * N1 + k1];
+    }
   });
 }
 
@@ -390,22 +419,23 @@ cudaError_t launch_k(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t
 
 template <int NX>
 size_t row_smem() {
-  return (size_t)(kRowThreads / Split<NX>::N1) * Split<NX>::N2 * (Split<NX>::N1 + 1) * sizeof(float2);
+  return (size_t)(kRowThreads / Lat<NX>::N1) * Lat<NX>::N2 * (Lat<NX>::N1 + 1) * sizeof(float2);
 }
 
 template <int NX>
 cudaError_t rows(bool adjoint, const ShParams& p, int chunks, cudaStream_t s) {
-  constexpr int RPI = kRowThreads / Split<NX>::N1;
+  constexpr int RPI = kRowThreads / Lat<NX>::N1;
   if (adjoint) return launch_k(rows_adj_kernel<NX>, dim3(p.ny / RPI, chunks), kRowThreads, row_smem<NX>(), s, p);
   return launch_k(rows_fwd_kernel<NX>, dim3(p.ny / RPI, p.nl), kRowThreads, row_smem<NX>(), s, p);
 }
 
 template <int NY>
 cudaError_t cols(bool adjoint, const ShParams& p, cudaStream_t s) {
-  const size_t smem = (size_t)NY * kTile * sizeof(float2);
-  const dim3 grid(p.nx / kTile, p.nl);
-  if (adjoint) return launch_k(cols_adj_kernel<NY>, grid, kTile * Split<NY>::N1, smem, s, p);
-  return launch_k(cols_fwd_kernel<NY>, grid, kTile * Split<NY>::N1, smem, s, p);
+  constexpr int TW = Lat<NY>::TW;
+  const size_t smem = (size_t)Lat<NY>::N2 * Lat<NY>::N1 * TW * sizeof(float2);
+  const dim3 grid(p.nx / TW, p.nl);
+  if (adjoint) return launch_k(cols_adj_kernel<NY>, grid, TW * Lat<NY>::N1, smem, s, p);
+  return launch_k(cols_fwd_kernel<NY>, grid, TW * Lat<NY>::N1, smem, s, p);
 }
 
 template <int NL>
@@ -419,7 +449,10 @@ cudaError_t rows_any(bool adj, const ShParams& p, int chunks, cudaStream_t s) {
     case 64: return rows<64>(adj, p, chunks, s);
     case 128: return rows<128>(adj, p, chunks, s);
     case 256: return rows<256>(adj, p, chunks, s);
+    case 384: return rows<384>(adj, p, chunks, s);
     case 512: return rows<512>(adj, p, chunks, s);
+    case 640: return rows<640>(adj, p, chunks, s);
+    case 768: return rows<768>(adj, p, chunks, s);
     case 1024: return rows<1024>(adj, p, chunks, s);
   }
   return cudaErrorInvalidValue;
@@ -430,7 +463,11 @@ cudaError_t cols_any(bool adj, const ShParams& p, cudaStream_t s) {
     case 64: return cols<64>(adj, p, s);
     case 128: return cols<128>(adj, p, s);
     case 256: return cols<256>(adj, p, s);
+    case 384: return cols<384>(adj, p, s);
     case 512: return cols<512>(adj, p, s);
+    case 640: return cols<640>(adj, p, s);
+    case 768: return cols<768>(adj, p, s);
+    case 1024: return cols<1024>(adj, p, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -440,7 +477,10 @@ cudaError_t axial_adj_any(const ShParams& p, cudaStream_t s) {
     case 16: return axial_adj<16>(p, s);
     case 32: return axial_adj<32>(p, s);
     case 64: return axial_adj<64>(p, s);
+    case 96: return axial_adj<96>(p, s);
     case 128: return axial_adj<128>(p, s);
+    case 160: return axial_adj<160>(p, s);
+    case 200: return axial_adj<200>(p, s);
     case 256: return axial_adj<256>(p, s);
     case 512: return axial_adj<512>(p, s);
   }
@@ -470,14 +510,38 @@ void build_pupil_table(int nx, int ny, double alpha, const double* coeffs, int n
     }
 }
 
-bool sharpness_supported(int nx, int ny, int nl) {
-  auto pow2_in = [](int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; };
-  return pow2_in(nx, 64, 1024) && pow2_in(ny, 64, 512) && pow2_in(nl, 16, 512);
+bool generic_lateral_supported(int nx, int ny) {
+  auto ok = [](int n) {
+    return n == 64 || n == 128 || n == 256 || n == 384 || n == 512 || n == 640 || n == 768 || n == 1024;
+  };
+  return ok(nx) && ok(ny);
+}
+
+bool sharpness_supported(int nx, int ny, int nl) { return generic_lateral_supported(nx, ny) && axial_supported(nl); }
+
+cudaError_t launch_lateral_generic(const Plan& pl, const uint16_t* frames, int ring_start, cudaStream_t s) {
+  char* ws = pl.ws;
+  ShParams p = {};
+  p.frames = frames;
+  p.xtab = (const Tap*)(ws + pl.off_xtab);
+  p.ytab = (const Tap*)(ws + pl.off_ytab);
+  p.cp = (const float2*)(ws + pl.off_cg);
+  p.twx = (const float2*)(ws + pl.off_twx);
+  p.twy = (const float2*)(ws + pl.off_twy);
+  p.twl = (const float2*)(ws + pl.off_twl);
+  p.F = (float2*)(ws + pl.off_F);
+  p.inter = (float2*)(ws + pl.off_inter);
+  p.nx = pl.nx; p.ny = pl.ny; p.nl = pl.nl;
+  p.x0 = pl.x0; p.y0 = pl.y0; p.wx = pl.wx; p.wy = pl.wy; p.ntx = pl.ntx;
+  p.ring_start = ring_start;
+  cudaError_t e = rows_any(false, p, 1, s);
+  if (e == cudaSuccess) e = cols_any(false, p, s);
+  return e;
 }
 
 cudaError_t launch_sharpness(const Plan& pl, const uint16_t* frames, float* vol, cudaStream_t s) {
   char* ws = pl.ws;
-  ShParams p;
+  ShParams p = {};
   p.frames = frames;
   p.xtab = (const Tap*)(ws + pl.off_xtab);
   p.ytab = (const Tap*)(ws + pl.off_ytab);

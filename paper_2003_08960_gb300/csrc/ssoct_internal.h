@@ -17,8 +17,8 @@ constexpr int kTile = 32;              // pixels per sweep-axis tile (one x-run)
 // FFT length N = N1 * N2 as the kernels split it: an N2-point DFT per thread,
 // a twiddle, an exchange through shared memory, N1-point DFTs (0 = not built).
 __host__ __device__ constexpr int split_n1(int n) {
-  return n == 16 ? 4 : n == 32 ? 4 : n == 64 ? 8 : n == 128 ? 8 : n == 256 ? 16
-       : n == 512 ? 16 : n == 1024 ? 32 : 0;
+  return n == 16 ? 4 : n == 32 ? 4 : n == 64 ? 8 : n == 96 ? 4 : n == 128 ? 8 : n == 160 ? 4 : n == 200 ? 5
+       : n == 256 ? 16 : n == 384 ? 16 : n == 512 ? 16 : n == 640 ? 32 : n == 768 ? 32 : n == 1024 ? 32 : 0;
 }
 
 // Separable linear-interpolation tap for one output coordinate of one frame
@@ -165,6 +165,10 @@ struct Plan {
   size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_ox, off_oy, off_twx, off_twy, off_twl;
   size_t off_tcb, off_ring, off_scratch, off_inter, ws_bytes;
   size_t off_cp = 0, off_F = 0, off_Q = 0, off_red = 0;  // SSOCT_FLAG_PUPIL regions
+  // Frame sizes the persistent lateral kernel does not compile (384, 640, 768)
+  // take the two-pass lateral path of sharpness.cu: chirp table and frame buffer.
+  bool generic = false;
+  size_t off_cg = 0;
   char* ws = nullptr;
   int device = -1;
   int num_sms = 0;
@@ -205,6 +209,10 @@ cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigne
 // off_red ([0] S1, [1] S2, [2] loss, [3] dL/dz, [4..18] dL/dc_1..15).
 constexpr int kShRedDoubles = 19;
 bool sharpness_supported(int nx, int ny, int nl);
+bool generic_lateral_supported(int nx, int ny);
+// Eq. 5 + Eq. 6 as a row pass and a column pass through the frame buffer at
+// off_F, for frames[(ring_start + t) mod nl]; writes the sweep-axis intermediate.
+cudaError_t launch_lateral_generic(const Plan& pl, const uint16_t* frames, int ring_start, cudaStream_t s);
 void build_pupil_table(int nx, int ny, double alpha, const double* coeffs, int ncoeffs, std::vector<float2>& out);
 cudaError_t launch_sharpness(const Plan& pl, const uint16_t* frames, float* vol, cudaStream_t s);
 // Dynamic shared memory of the lateral kernel for a plan (bytes).

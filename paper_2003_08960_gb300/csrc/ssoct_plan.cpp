@@ -203,7 +203,9 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   ssoct_window w = win ? *win : ssoct_window{0, 0, nx, ny};
   if (w.x0 < 0 || w.y0 < 0 || w.wx < 1 || w.wy < 1 || w.x0 + w.wx > nx || w.y0 + w.wy > ny)
     return SSOCT_EINVAL;
-  if (!lateral_supported(nx, ny) || !axial_supported(nlambda)) return SSOCT_EUNSUPPORTED;
+  if (!axial_supported(nlambda)) return SSOCT_EUNSUPPORTED;
+  const bool generic = !lateral_supported(nx, ny);  // two-pass lateral path for the other sizes
+  if (generic && !generic_lateral_supported(nx, ny)) return SSOCT_EUNSUPPORTED;
   if ((flags & SSOCT_FLAG_TC_AXIAL) && !axial_tc_supported(nlambda)) return SSOCT_EUNSUPPORTED;
   if ((flags & SSOCT_FLAG_PUPIL) && !sharpness_supported(nx, ny, nlambda)) return SSOCT_EUNSUPPORTED;
 
@@ -213,6 +215,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.nx = nx; p.ny = ny; p.nl = nlambda;
   p.x0 = w.x0; p.y0 = w.y0; p.wx = w.wx; p.wy = w.wy;
   p.flags = flags;
+  p.generic = generic;
   p.pitch = pitch_m; p.z = z_m;
   p.lambdas.assign(lambda_m, lambda_m + nlambda);
   p.lambda1 = lambda_m[0];
@@ -284,7 +287,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
       if (rows > st) st = rows;
     }
   p.stage_rows = st;
-  if (lateral_smem_bytes(p) > 227u * 1024u) {
+  if (!generic && lateral_smem_bytes(p) > 227u * 1024u) {
     delete h;
     return SSOCT_EUNSUPPORTED;  // rescale ratio too far from 1 for the staging buffer
   }
@@ -304,12 +307,13 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_twl = take(sizeof(float2) * p.twl.size());
   p.off_tcb = take(sizeof(unsigned short) * p.tcb.size());
   p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
-  p.off_scratch = take(sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
+  p.off_scratch = take(generic ? 0 : sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
   p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
+  if (generic) p.off_cg = take(sizeof(float2) * (size_t)nx * ny);
+  if (generic || (flags & SSOCT_FLAG_PUPIL)) p.off_F = take(sizeof(float2) * (size_t)nlambda * ny * nx);
   if (flags & SSOCT_FLAG_PUPIL) {
     const size_t chunks = (size_t)(nlambda + p.sh_tpc - 1) / p.sh_tpc;
     p.off_cp = take(sizeof(float2) * (size_t)nx * ny);
-    p.off_F = take(sizeof(float2) * (size_t)nlambda * ny * nx);
     p.off_Q = take(sizeof(float2) * chunks * ny * nx);
     p.off_red = take(sizeof(double) * kShRedDoubles);
   }
@@ -374,7 +378,15 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
   p.ws = ws;
   p.stream_count = 0;
   p.lat_upto = -1;
-  if (!encode_scratch_map(p) || !encode_inter_map_at(p, p.ws + p.off_inter, p.tmap_inter)) {
+  if (p.generic) {
+    std::vector<float2> cg;
+    build_pupil_table(p.nx, p.ny, p.alpha, nullptr, 0, cg);  // the input chirp alone
+    e = cudaMemcpy(ws + p.off_cg, cg.data(), sizeof(float2) * cg.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      p.ws = nullptr;
+      return cuda_fail(&p, e, "chirp table upload");
+    }
+  } else if (!encode_scratch_map(p) || !encode_inter_map_at(p, p.ws + p.off_inter, p.tmap_inter)) {
     p.ws = nullptr;
     return fail(&p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the scratch ring or the intermediate");
   }
@@ -484,7 +496,7 @@ static ssoct_status launch_lateral_pass(Plan& p, const LateralParams& lp, cudaSt
     p.events_used += 3;
     cudaEventRecord((*ev)[0], s);
   }
-  e = launch_lateral(p, lp, s);
+  e = p.generic ? launch_lateral_generic(p, lp.frames, lp.ring_start, s) : launch_lateral(p, lp, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "lateral kernel launch");
   if (*ev) cudaEventRecord((*ev)[1], s);
   return SSOCT_OK;
@@ -546,6 +558,7 @@ ssoct_status ssoct_reconstruct_sliding(ssoct_plan h, float* vol_dev, void* compl
   if (!h) return SSOCT_EINVAL;
   Plan& p = h->p;
   if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
+  if (p.generic) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need a frame size of the persistent lateral kernel");
   if (p.stream_count < p.nl) return fail(&p, SSOCT_ENOTREADY, "fewer than nlambda frames pushed");
   if (!vol_dev || ((uintptr_t)vol_dev % 16) || ((uintptr_t)complex_dev % 16))
     return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");

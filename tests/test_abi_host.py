@@ -83,7 +83,7 @@ def test_pupil_plan_validation(ss):
     refuses without the flag, without a workspace or with bad coefficients."""
     st, h = ss.ssoct_create_plan(96, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_PUPIL)
     assert st == ss.SSOCT_EUNSUPPORTED
-    st, h = ss.ssoct_create_plan(64, 1024, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_PUPIL)
+    st, h = ss.ssoct_create_plan(64, 1000, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_PUPIL)
     assert st == ss.SSOCT_EUNSUPPORTED
     st, plain = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM)
     st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_PUPIL)
@@ -146,3 +146,27 @@ def test_binding_refuses_without_gpu(ss):
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError, match="CUDA device"):
         ss.Plan(64, 64, 32, 20e-6, 0.3, LAM)
+
+
+def test_mixed_radix_plan_sizes(ss):
+    """Frame sizes outside the persistent kernel's list take the two-pass lateral
+    path (its frame buffer shows in the workspace); sweep lengths 96, 160, 200
+    are compiled; other lengths and sizes are refused."""
+    def ws(nx, ny, nl):
+        lam = np.linspace(800e-9, 850e-9, nl)
+        st, h = ss.ssoct_create_plan(nx, ny, nl, 20e-6, 0.3, lam)
+        if st != ss.SSOCT_OK:
+            return st, None
+        _, b = ss.ssoct_workspace_size(h)
+        ss.ssoct_destroy_plan(h)
+        return st, b
+    for nx, ny, nl in [(384, 384, 96), (640, 640, 160), (768, 768, 200), (640, 384, 32), (256, 256, 96)]:
+        st, b = ws(nx, ny, nl)
+        assert st == ss.SSOCT_OK, (nx, ny, nl)
+    for nx, ny, nl in [(100, 64, 32), (384, 384, 100), (1280, 1280, 32), (256, 256, 48)]:
+        st, _ = ws(nx, ny, nl)
+        assert st == ss.SSOCT_EUNSUPPORTED, (nx, ny, nl)
+    # generic plan: no scratch ring, a frame buffer [nl][ny][nx] and a chirp table instead
+    _, b_gen = ws(384, 384, 32)
+    frames = 32 * 384 * 384
+    assert b_gen >= frames * 2 + frames * 8 + 384 * 384 * 8

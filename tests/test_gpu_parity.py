@@ -288,3 +288,30 @@ def test_tc_axial_paper_size_1024x1024x256(ss):
     plan, vol, cplx, ref = _run(ss, w, method="fft", flags=ss.SSOCT_FLAG_TC_AXIAL)
     err_v, err_p = _check_tc(vol, cplx, ref)
     print(f"TC axial 1024x1024x256: complex rel L2 {err_v:.3e}, |V|^2 rel L2 {err_p:.3e}")
+
+
+# Mixed radix (2/3/5): frame sizes 384, 640, 768 take the two-pass lateral path,
+# sweep lengths 96, 160, 200 the axial kernel with N1 = 4, 4, 5.
+@pytest.mark.parametrize("shape,window", [((384, 384, 96), None), ((640, 640, 160), (100, 60, 400, 300)),
+                                          ((640, 384, 32), None), ((256, 256, 200), None),
+                                          ((768, 768, 200), (0, 0, 768, 200))])
+def test_mixed_radix_sizes(ss, shape, window):
+    nx, ny, nl = shape
+    w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=nx + ny + nl)
+    plan, vol, cplx, ref = _run(ss, w, window=window, method="fft")
+    err = _check(vol, cplx, ref, quadrant=window is None)
+    print(f"{shape} window={window}: complex rel L2 {err:.3e}")
+
+
+def test_mixed_radix_ring_path(ss):
+    w = synth.workload("custom", nx=384, ny=384, nlambda=96, kind="points", seed=4)
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    ref = plan.reconstruct(_dev(w.frames))
+    plan.push(_dev(w.frames[:40]), first_seq=0)
+    plan.push(_dev(w.frames), first_seq=40)     # the gate (last 96 frames) is the sweep, from ring slot 40
+    v = plan.reconstruct_ring()
+    torch.cuda.synchronize()
+    assert torch.equal(v, ref)
+    with pytest.raises(ss.SsoctError) as e:
+        plan.reconstruct_sliding()
+    assert e.value.status == ss.SSOCT_EUNSUPPORTED
