@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct ssoct_plan_s* ssoct_plan;
+typedef struct ssoct_batch_s* ssoct_batch;
 
 /* Off-axis window in hologram-plane pixels: columns x0 .. x0+wx-1, rows
  * y0 .. y0+wy-1 of the Nx x Ny hologram computed by Eq. 6.  {0, 0, nx, ny} is
@@ -253,6 +254,59 @@ SSOCT_API const char* ssoct_status_string(ssoct_status s);
 
 /* Release the plan's host memory.  The workspace stays the caller's. */
 SSOCT_API void ssoct_destroy_plan(ssoct_plan plan);
+
+/* Autotuner.  Chosen schedule of a plan (see ssoct_autotune). */
+typedef struct {
+  int lag;         /* steps between a frame's row items and its column items in the lateral kernel's queue */
+  int ring_slots;  /* L2 scratch-ring slots in use (<= the workspace's, ring_slots of ssoct_plan_info) */
+  int tc_axial;    /* 1: axial pass on the tensor cores (SSOCT_FLAG_TC_AXIAL's form) */
+  double ms;       /* measured time of one reconstruction with this choice */
+  int from_cache;  /* 1: read from the cache file, nothing timed */
+  int candidates;  /* choices timed */
+} ssoct_tune_t;
+
+/* Time the plan's candidate schedules on frames_dev (reconstructing into the
+ * scratch volume vol_dev, [nlambda][wy][wx] float) and keep the fastest: the
+ * lateral kernel's (lag, ring slots) with lag 1..3 and lag + 2 <= slots <= the
+ * workspace's slots, times the FP32 and tensor-core axial forms when nlambda is
+ * 256.  With cache_path (NULL = none), a JSON file holding one entry per line
+ * keyed by GPU name, SM count, frame size, sweep length and window is read
+ * first (a hit applies the stored choice without timing) and updated after
+ * timing.  The choice stays with the plan; results are the same up to the
+ * axial form's rounding.  Synchronises `stream`.  EINVAL if the cache cannot be
+ * written (the choice is still applied). */
+SSOCT_API ssoct_status ssoct_autotune(ssoct_plan plan, const uint16_t* frames_dev, float* vol_dev,
+                                      const char* cache_path, void* stream, ssoct_tune_t* result);
+
+/* Batches: several volumes of different sizes (one plan each, e.g. 256^2 x 64
+ * up to 1024^2 x 256) reconstructed by one CUDA graph launch.  The paper
+ * reconstructs one sweep at a time; batching is this library's.
+ * ssoct_batch_create: n distinct plans, each with its workspace set and with
+ * profiling and stall injection off (EINVAL otherwise).  Creates one stream and
+ * one event per plan; host memory and CUDA objects are the batch's until
+ * ssoct_batch_destroy, the plans stay the caller's and must outlive it. */
+SSOCT_API ssoct_status ssoct_batch_create(const ssoct_plan* plans, int n, ssoct_batch* out);
+
+/* Reconstruct plan i's sweep frames_dev[i] into vol_dev[i] (as
+ * ssoct_reconstruct_frames, no complex output) for all i, ordered after the
+ * work already on `stream`; returns without waiting.  The first call on a set
+ * of pointers captures all plans' kernels into a graph (each plan on its own
+ * forked stream); later calls on the same pointers relaunch it (one
+ * cudaGraphLaunch).  Different pointers recapture. */
+SSOCT_API ssoct_status ssoct_batch_run(ssoct_batch b, const uint16_t* const* frames_dev, float* const* vol_dev,
+                                       void* stream);
+
+/* Wait for `stream` and report what each plan's kernels recorded (as ssoct_sync). */
+SSOCT_API ssoct_status ssoct_batch_sync(ssoct_batch b, void* stream);
+
+/* Number of graph captures so far (-1 for NULL). */
+SSOCT_API int ssoct_batch_captures(ssoct_batch b);
+
+/* Description of the last error of a batch call. */
+SSOCT_API const char* ssoct_batch_last_error(ssoct_batch b);
+
+/* Release the batch (not its plans). */
+SSOCT_API void ssoct_batch_destroy(ssoct_batch b);
 
 #ifdef __cplusplus
 }

@@ -268,6 +268,14 @@ class Plan:
     def sync(self, stream=None) -> None:
         _check(ssoct_sync(self._h, _stream_ptr(stream)), self._h, "sync")
 
+    def autotune(self, frames, cache_path=None, stream=None) -> dict:
+        """Time this plan's candidate schedules on `frames` and keep the fastest
+        (see ssoct_autotune); returns the choice."""
+        vol, _ = self.empty_volume()
+        st, r = ssoct_autotune(self._h, frames.data_ptr(), vol.data_ptr(), cache_path, _stream_ptr(stream))
+        _check(st, self._h, "autotune")
+        return r
+
     def sharpness(self, frames, coeffs: Sequence[float], z_m: float, out=None, stream=None):
         """(loss, grad[16], volume) of the pupil-corrected reconstruction: grad[0] =
         dL/dz, grad[j] = dL/dc_j (needs a plan made with SSOCT_FLAG_PUPIL)."""
@@ -276,3 +284,73 @@ class Plan:
         st, res = ssoct_sharpness(self._h, frames.data_ptr(), vol.data_ptr(), _stream_ptr(stream))
         _check(st, self._h, "sharpness")
         return float(res[0]), res[1:].copy(), vol
+
+
+def ssoct_autotune(plan, frames_ptr: int, vol_ptr: int, cache_path, stream: int):
+    """Returns (status, dict with lag, ring_slots, tc_axial, ms, from_cache, candidates)."""
+    r = _abi.ssoct_tune_t()
+    path = None if cache_path is None else str(cache_path).encode()
+    st = _abi.lib().ssoct_autotune(plan, C.c_void_p(frames_ptr), C.c_void_p(vol_ptr), path, C.c_void_p(stream),
+                                   C.byref(r))
+    return st, {k: getattr(r, k) for k, _ in r._fields_}
+
+
+def ssoct_batch_create(plans):
+    """Returns (status, batch handle or None) for a list of plan handles."""
+    arr = (_abi.ssoct_plan * len(plans))(*plans)
+    out = C.c_void_p()
+    st = _abi.lib().ssoct_batch_create(arr, len(plans), C.byref(out))
+    return st, (out.value if st == SSOCT_OK else None)
+
+
+def ssoct_batch_run(batch, frame_ptrs, vol_ptrs, stream: int) -> int:
+    n = len(frame_ptrs)
+    fa = (C.c_void_p * n)(*frame_ptrs)
+    va = (C.c_void_p * n)(*vol_ptrs)
+    return _abi.lib().ssoct_batch_run(batch, fa, va, C.c_void_p(stream))
+
+
+def ssoct_batch_sync(batch, stream: int) -> int:
+    return _abi.lib().ssoct_batch_sync(batch, C.c_void_p(stream))
+
+
+def ssoct_batch_captures(batch) -> int:
+    return _abi.lib().ssoct_batch_captures(batch)
+
+
+def ssoct_batch_last_error(batch) -> str:
+    return _abi.lib().ssoct_batch_last_error(batch).decode()
+
+
+def ssoct_batch_destroy(batch) -> None:
+    _abi.lib().ssoct_batch_destroy(batch)
+
+
+class Batch:
+    """Several plans reconstructed by one CUDA graph launch (see ssoct_batch_run)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        st, self._b = ssoct_batch_create([p.handle for p in self.plans])
+        if st != SSOCT_OK:
+            raise SsoctError(st, "batch_create")
+
+    def run(self, frames, vols, stream=None) -> None:
+        st = ssoct_batch_run(self._b, [f.data_ptr() for f in frames], [v.data_ptr() for v in vols],
+                             _stream_ptr(stream))
+        if st != SSOCT_OK:
+            raise SsoctError(st, "batch_run " + ssoct_batch_last_error(self._b))
+
+    def sync(self, stream=None) -> None:
+        st = ssoct_batch_sync(self._b, _stream_ptr(stream))
+        if st != SSOCT_OK:
+            raise SsoctError(st, "batch_sync " + ssoct_batch_last_error(self._b))
+
+    @property
+    def captures(self) -> int:
+        return ssoct_batch_captures(self._b)
+
+    def __del__(self):
+        if getattr(self, "_b", None):
+            ssoct_batch_destroy(self._b)
+            self._b = None

@@ -50,6 +50,11 @@ class ssoct_plan_info_t(C.Structure):
     ]
 
 
+class ssoct_tune_t(C.Structure):
+    _fields_ = [("lag", C.c_int), ("ring_slots", C.c_int), ("tc_axial", C.c_int), ("ms", C.c_double),
+                ("from_cache", C.c_int), ("candidates", C.c_int)]
+
+
 ssoct_plan = C.c_void_p
 
 # name -> (restype, argtypes); mirrors include/ssoct.h
@@ -77,6 +82,14 @@ SIGNATURES = {
     "ssoct_last_error": (C.c_char_p, [ssoct_plan]),
     "ssoct_status_string": (C.c_char_p, [C.c_int]),
     "ssoct_destroy_plan": (None, [ssoct_plan]),
+    "ssoct_autotune": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.c_char_p, C.c_void_p,
+                                 C.POINTER(ssoct_tune_t)]),
+    "ssoct_batch_create": (C.c_int, [C.POINTER(ssoct_plan), C.c_int, C.POINTER(C.c_void_p)]),
+    "ssoct_batch_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
+    "ssoct_batch_sync": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ssoct_batch_captures": (C.c_int, [C.c_void_p]),
+    "ssoct_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "ssoct_batch_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None

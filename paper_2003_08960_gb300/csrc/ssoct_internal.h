@@ -161,6 +161,8 @@ struct Plan {
   int wxp, ntx;
   int stage_rows;
   LateralSchedule sch;
+  int slots_alloc = 0;       // scratch-ring slots the workspace holds (sch.slots <= slots_alloc)
+  bool use_tc = false;       // axial pass on the tensor cores (flag, or the autotuner's choice)
   // workspace layout (byte offsets)
   size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_ox, off_oy, off_twx, off_twy, off_twl;
   size_t off_tcb, off_ring, off_scratch, off_inter, ws_bytes;

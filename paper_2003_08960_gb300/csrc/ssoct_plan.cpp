@@ -262,7 +262,8 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.twx = twiddles(nx, p.n1x, p.n2x, +1);
   p.twy = twiddles(ny, p.n1y, p.n2y, +1);
   p.twl = twiddles(nlambda, p.n1l, p.n2l, -1);
-  if (flags & SSOCT_FLAG_TC_AXIAL) axial_tc_table(p.tcb);
+  if (axial_tc_supported(nlambda)) axial_tc_table(p.tcb);  // kept for every such plan: the autotuner may switch forms
+  p.use_tc = (flags & SSOCT_FLAG_TC_AXIAL) != 0;
 
   // Work decomposition of the lateral kernel.
   p.rows_per_item = kThreads / p.n1x;
@@ -277,6 +278,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   // a row item of frame f reuses the slot of frame f - slots, whose last column
   // items were taken four steps earlier: enough slack that the wait is rare
   p.sch.slots = p.sch.lag + 4;
+  p.slots_alloc = p.sch.slots;
   // input rows a row item stages: from the first row's base to the last row's base + 1
   int st = 0;
   for (int t = 0; t < nlambda; ++t)
@@ -514,7 +516,7 @@ static ssoct_status launch_axial_pass(Plan& p, float* vol, void* cplx, cudaStrea
   ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
   ap.power_scale = (float)(p.alpha * p.alpha);
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
-  cudaError_t e = (p.flags & SSOCT_FLAG_TC_AXIAL)
+  cudaError_t e = p.use_tc
                       ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb),
                                         &((Counters*)(ws + p.off_ctr))->err, s)
                       : launch_axial(p, ap, s);

@@ -75,7 +75,7 @@ def test_create_plan_validation(ss):
     st, h = ss.ssoct_create_plan(64, 64, 256, 20e-6, 0.3, lam256)
     st, bytes_plain = ss.ssoct_workspace_size(h)
     ss.ssoct_destroy_plan(h)
-    assert bytes_tc - bytes_plain == 4096      # the BF16 hi / lo 32 x 32 operand table
+    assert bytes_tc == bytes_plain      # every 256-frame plan keeps the BF16 operand table (the autotuner may switch)
 
 
 def test_pupil_plan_validation(ss):
@@ -170,3 +170,15 @@ def test_mixed_radix_plan_sizes(ss):
     _, b_gen = ws(384, 384, 32)
     frames = 32 * 384 * 384
     assert b_gen >= frames * 2 + frames * 8 + 384 * 384 * 8
+
+
+def test_batch_and_autotune_refuse_without_workspace(ss):
+    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM)
+    assert st == ss.SSOCT_OK
+    st, b = ss.ssoct_batch_create([h])
+    assert st == ss.SSOCT_ENOMEM and b is None
+    st, b = ss.ssoct_batch_create([])
+    assert st == ss.SSOCT_EINVAL
+    st, r = ss.ssoct_autotune(h, 0, 0, None, 0)
+    assert st == ss.SSOCT_ENOMEM
+    ss.ssoct_destroy_plan(h)
