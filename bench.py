@@ -192,6 +192,12 @@ def run_ssoct(args):
     frames = torch.from_numpy(w.frames.view(np.int16)).cuda()
     vol, _ = plan.empty_volume()
     nl, wy, wx = plan.volume_shape()
+    # schedule of the persistent lateral kernel (and axial form, if --tc-axial
+    # is not forcing it) chosen by the library's autotuner on these frames
+    tune = None
+    if not args.no_autotune and not args.tc_axial:
+        tune = plan.autotune(frames, None, stream)
+    tc_main = args.tc_axial or bool(tune and tune["tc_axial"])
     xy = torch.empty((wy, wx), dtype=torch.float32, device="cuda")
     xz = torch.empty((nl, wx), dtype=torch.float32, device="cuda")
     yz = torch.empty((nl, wy), dtype=torch.float32, device="cuda")
@@ -239,9 +245,10 @@ def run_ssoct(args):
     ms, value = aggregate(ms, voxels, world, dist if world > 1 else None, device="cuda")
 
     peak, peak_kind = _peaks()
-    tc = None if (args.tc_axial or args.no_e2e) else _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak)
+    tc = None if (tc_main or args.no_e2e) else _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak)
     sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if not args.no_e2e else None
     aberration = _aberration(args, ss, torch, synth, stream) if not args.no_e2e else None
+    batched = _batched(args, ss, torch, synth, w, frames, stream) if not args.no_e2e else None
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
     e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
@@ -254,7 +261,7 @@ def run_ssoct(args):
     for k in kernels.values():
         k["frac"] = k["GBps"] / peak
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    traffic = _traffic("axial_tc" if (args.tc_axial and dom == "axial") else dom)
+    traffic = _traffic("axial_tc" if (tc_main and dom == "axial") else dom)
     whole_bytes = lat_bytes + ax_bytes
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -264,7 +271,9 @@ def run_ssoct(args):
         "config": {"workload": f"{w.nx}x{w.ny}x{nl} sweep, uint16 frames resident in HBM, full window, "
                                "|V|^2 volume + 3 cuts per step",
                    "window": [0, 0, wx, wy],
-                   "form": "tensor-core axial (bf16 hi+lo, fp32 accumulate)" if args.tc_axial else "fp32 (paper order)",
+                   "schedule": ({k: tune[k] for k in ("lag", "ring_slots", "tc_axial")} if tune
+                                else "plan default (lag 2, 6 ring slots)"),
+                   "form": "tensor-core axial (bf16 hi+lo, fp32 accumulate)" if tc_main else "fp32 (paper order)",
                    "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["GBps"], "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
@@ -277,6 +286,7 @@ def run_ssoct(args):
         "sliding": sliding,
         "tc_axial": tc,
         "aberration": aberration,
+        "batched": batched,
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
@@ -460,6 +470,61 @@ def _aberration(args, ss, torch, synth, stream, steps=10):
             "note": "host wall time per ssoct_sharpness call (forward + adjoint + 17 doubles read back)"}
 
 
+BATCH_SHAPES = [(256, 256, 64), (384, 384, 96), (512, 512, 128), (512, 512, 128), (640, 640, 160),
+                (768, 768, 200), (1024, 1024, 256), (1024, 1024, 256)]
+
+
+def _batched(args, ss, torch, synth, w_1024, frames_1024, stream, steps=10):
+    """Eight uneven volumes (805.8 Mvoxel) reconstructed by one graph launch per
+    step (ssoct_batch_run), against the same plans run one after another."""
+    plans, frames, vols = [], [], []
+    for i, (nx, ny, nl) in enumerate(BATCH_SHAPES):
+        if (nx, ny, nl) == (w_1024.nx, w_1024.ny, w_1024.nlambda):
+            w, f = w_1024, frames_1024
+        else:
+            w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=10 + i)
+            f = torch.from_numpy(w.frames.view(np.int16)).cuda()
+        plans.append(ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas))
+        frames.append(f)
+        vols.append(plans[-1].empty_volume()[0])
+    voxels = sum(nx * ny * nl for nx, ny, nl in BATCH_SHAPES)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    lanes = {}
+    for n_lanes in (1, 2, 4):
+        batch = ss.Batch(plans, lanes=n_lanes)
+        lanes[n_lanes] = timed(lambda: batch.run(frames, vols, stream=stream))
+        batch.sync(stream)
+        captures = batch.captures
+        del batch
+    best = min(lanes, key=lanes.get)
+    ms_batch = lanes[best]
+
+    def separate():
+        for p, f, v in zip(plans, frames, vols):
+            p.reconstruct(f, out=(v, None), stream=stream)
+
+    ms_sep = timed(separate)
+    return {"volumes": [f"{nx}x{ny}x{nl}" for nx, ny, nl in BATCH_SHAPES], "voxels": voxels,
+            "ms_per_batch": ms_batch, "Gvoxel_per_s": voxels / (ms_batch * 1e-3) / 1e9,
+            "ms_separate": ms_sep, "Gvoxel_per_s_separate": voxels / (ms_sep * 1e-3) / 1e9,
+            "lanes": best, "ms_by_lanes": lanes, "graph_captures": captures,
+            "form": "one CUDA graph launch per batch, volume i on stream lane i mod lanes; "
+                    "384/640/768 frames take the two-pass lateral path"}
+
+
 def _traffic(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
     current kernel source (null otherwise)."""
@@ -483,6 +548,7 @@ def main():
     ap.add_argument("--impl", default="ssoct", choices=["ssoct", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default schedule")
     ap.add_argument("--tc-axial", action="store_true", help="time the tensor-core axial form as the main line "
                                                             "(profiling captures)")
     ap.add_argument("--size", default=None, help="NXxNYxNLAMBDA instead of the 1024x1024x256 workload "

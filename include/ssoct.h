@@ -69,9 +69,8 @@ typedef enum {
  * SSOCT_EUNSUPPORTED at plan creation). */
 #define SSOCT_FLAG_TC_AXIAL 0x2u
 /* Reserve the workspace of the aberration path (ssoct_set_pupil, ssoct_sharpness):
- * the c P table, one complex frame per wavelength, partial sums.  Sizes: nx a
- * power of two in 64..1024, ny in 64..512, nlambda in 16..512 (else
- * SSOCT_EUNSUPPORTED at plan creation). */
+ * the c P table, one complex frame per wavelength, partial sums.  Any compiled
+ * frame size and sweep length (see ssoct_create_plan). */
 #define SSOCT_FLAG_PUPIL 0x4u
 
 /* Read-only facts about a plan. */
@@ -198,8 +197,9 @@ SSOCT_API ssoct_status ssoct_reconstruct_sliding(ssoct_plan plan, float* vol_dev
  * radius (pixel centre N/2) over min(nx, ny) d / 2, continued outside the disk.
  * Sets the coefficients (radians; coeffs[j - 1] = c_j, ncoeffs 0..15, missing
  * ones 0) and the distance z_m used by ssoct_sharpness (the plan's own z stays
- * in use for the other calls).  Needs SSOCT_FLAG_PUPIL and a workspace; blocks
- * until the table is in device memory. */
+ * in use for the other calls).  Needs SSOCT_FLAG_PUPIL and a workspace.  Host
+ * only: the next ssoct_sharpness builds the c P table on the device (FP64
+ * phases, one rounding to FP32). */
 SSOCT_API ssoct_status ssoct_set_pupil(ssoct_plan plan, const double* coeffs, int ncoeffs, double z_m);
 
 /* Sharpness of the pupil-corrected volume and its gradient, by one forward and
@@ -282,17 +282,19 @@ SSOCT_API ssoct_status ssoct_autotune(ssoct_plan plan, const uint16_t* frames_de
  * up to 1024^2 x 256) reconstructed by one CUDA graph launch.  The paper
  * reconstructs one sweep at a time; batching is this library's.
  * ssoct_batch_create: n distinct plans, each with its workspace set and with
- * profiling and stall injection off (EINVAL otherwise).  Creates one stream and
- * one event per plan; host memory and CUDA objects are the batch's until
- * ssoct_batch_destroy, the plans stay the caller's and must outlive it. */
-SSOCT_API ssoct_status ssoct_batch_create(const ssoct_plan* plans, int n, ssoct_batch* out);
+ * profiling and stall injection off (EINVAL otherwise).  lanes = streams the
+ * graph spreads the volumes over (volume i on lane i mod lanes; 1 = back to
+ * back, 0 = one per volume).  Creates one stream and one event per lane; host
+ * memory and CUDA objects are the batch's until ssoct_batch_destroy, the plans
+ * stay the caller's and must outlive it. */
+SSOCT_API ssoct_status ssoct_batch_create(const ssoct_plan* plans, int n, int lanes, ssoct_batch* out);
 
 /* Reconstruct plan i's sweep frames_dev[i] into vol_dev[i] (as
  * ssoct_reconstruct_frames, no complex output) for all i, ordered after the
  * work already on `stream`; returns without waiting.  The first call on a set
- * of pointers captures all plans' kernels into a graph (each plan on its own
- * forked stream); later calls on the same pointers relaunch it (one
- * cudaGraphLaunch).  Different pointers recapture. */
+ * of pointers captures all plans' kernels into a graph (on its lanes); later
+ * calls on the same pointers relaunch it (one cudaGraphLaunch).  Different
+ * pointers recapture. */
 SSOCT_API ssoct_status ssoct_batch_run(ssoct_batch b, const uint16_t* const* frames_dev, float* const* vol_dev,
                                        void* stream);
 

@@ -295,11 +295,11 @@ def ssoct_autotune(plan, frames_ptr: int, vol_ptr: int, cache_path, stream: int)
     return st, {k: getattr(r, k) for k, _ in r._fields_}
 
 
-def ssoct_batch_create(plans):
+def ssoct_batch_create(plans, lanes: int = 1):
     """Returns (status, batch handle or None) for a list of plan handles."""
     arr = (_abi.ssoct_plan * len(plans))(*plans)
     out = C.c_void_p()
-    st = _abi.lib().ssoct_batch_create(arr, len(plans), C.byref(out))
+    st = _abi.lib().ssoct_batch_create(arr, len(plans), lanes, C.byref(out))
     return st, (out.value if st == SSOCT_OK else None)
 
 
@@ -329,9 +329,9 @@ def ssoct_batch_destroy(batch) -> None:
 class Batch:
     """Several plans reconstructed by one CUDA graph launch (see ssoct_batch_run)."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, lanes: int = 1):
         self.plans = list(plans)
-        st, self._b = ssoct_batch_create([p.handle for p in self.plans])
+        st, self._b = ssoct_batch_create([p.handle for p in self.plans], lanes)
         if st != SSOCT_OK:
             raise SsoctError(st, "batch_create")
 

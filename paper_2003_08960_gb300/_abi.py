@@ -84,7 +84,7 @@ SIGNATURES = {
     "ssoct_destroy_plan": (None, [ssoct_plan]),
     "ssoct_autotune": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.c_char_p, C.c_void_p,
                                  C.POINTER(ssoct_tune_t)]),
-    "ssoct_batch_create": (C.c_int, [C.POINTER(ssoct_plan), C.c_int, C.POINTER(C.c_void_p)]),
+    "ssoct_batch_create": (C.c_int, [C.POINTER(ssoct_plan), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     "ssoct_batch_run": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p]),
     "ssoct_batch_sync": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ssoct_batch_captures": (C.c_int, [C.c_void_p]),

@@ -1,8 +1,10 @@
 // Batched reconstruction of several volumes of different sizes (one plan each)
 // as one CUDA graph.  The first run on a set of frame / volume pointers captures
-// every plan's kernels (lateral pass, axial pass) with each plan on its own
-// forked stream, so that small volumes overlap large ones; later runs on the
-// same pointers relaunch the instantiated graph with one call.
+// every plan's kernels (lateral pass, axial pass), volume i on lane (stream)
+// i mod lanes; later runs on the same pointers relaunch the instantiated graph
+// with one call.  One lane runs the volumes back to back; more lanes let a
+// volume's kernels overlap another's, which pays off only where kernels leave
+// SMs idle (the persistent lateral kernel takes every SM).
 #include <string>
 #include <vector>
 
@@ -40,10 +42,11 @@ void drop_graph(ssoct_batch b) {
 
 using namespace ssoct;
 
-extern "C" ssoct_status ssoct_batch_create(const ssoct_plan* plans, int n, ssoct_batch* out) {
+extern "C" ssoct_status ssoct_batch_create(const ssoct_plan* plans, int n, int lanes, ssoct_batch* out) {
   if (!out) return SSOCT_EINVAL;
   *out = nullptr;
-  if (!plans || n < 1) return SSOCT_EINVAL;
+  if (!plans || n < 1 || lanes < 0) return SSOCT_EINVAL;
+  if (lanes == 0 || lanes > n) lanes = n;
   for (int i = 0; i < n; ++i) {
     if (!plans[i]) return SSOCT_EINVAL;
     const Plan& p = plan_of(plans[i]);
@@ -57,7 +60,7 @@ extern "C" ssoct_status ssoct_batch_create(const ssoct_plan* plans, int n, ssoct
   b->plans.assign(plans, plans + n);
   cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
-  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+  for (int i = 0; i < lanes && e == cudaSuccess; ++i) {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -93,13 +96,14 @@ extern "C" ssoct_status ssoct_batch_run(ssoct_batch b, const uint16_t* const* fr
     if (e != cudaSuccess) return batch_fail(b, SSOCT_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
     ssoct_status st = SSOCT_OK;
     e = cudaEventRecord(b->fork, o);
-    for (int i = 0; i < n && e == cudaSuccess && st == SSOCT_OK; ++i) {
-      e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-      if (e != cudaSuccess) break;
-      st = ssoct_reconstruct_frames(b->plans[i], frames_dev[i], vol_dev[i], nullptr, b->streams[i]);
-      if (st != SSOCT_OK) break;
-      e = cudaEventRecord(b->done[i], b->streams[i]);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(o, b->done[i], 0);
+    const int lanes = (int)b->streams.size();
+    for (int l = 0; l < lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->streams[l], b->fork, 0);
+    // volume i runs on lane i mod lanes, after the lane's previous volume
+    for (int i = 0; i < n && e == cudaSuccess && st == SSOCT_OK; ++i)
+      st = ssoct_reconstruct_frames(b->plans[i], frames_dev[i], vol_dev[i], nullptr, b->streams[i % lanes]);
+    for (int l = 0; l < lanes && e == cudaSuccess && st == SSOCT_OK; ++l) {
+      e = cudaEventRecord(b->done[l], b->streams[l]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(o, b->done[l], 0);
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(o, &g);

@@ -510,6 +510,50 @@ void build_pupil_table(int nx, int ny, double alpha, const double* coeffs, int n
     }
 }
 
+namespace {
+
+struct PupilParams {
+  float2* cp;
+  int nx, ny, ncoeffs;
+  double alpha;
+  double c[15];
+};
+
+// c P per sensor pixel, the device twin of build_pupil_table: phases reduced in
+// units of pi in float64, one rounding to float32 at the end.
+__global__ void __launch_bounds__(256) pupil_table_kernel(const __grid_constant__ PupilParams p) {
+  const size_t npix = (size_t)p.nx * p.ny;
+  const double inv_radius = 2.0 / (double)min(p.nx, p.ny);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(i % p.nx), l = (int)(i / p.nx);
+    const double dx = n - p.nx / 2.0, dy = l - p.ny / 2.0;
+    double turns = -(fmod(p.alpha * dx * dx, 2.0) + (double)(n & 1)) - (fmod(p.alpha * dy * dy, 2.0) + (double)(l & 1));
+    const double rp = sqrt(dx * dx + dy * dy);
+    double z[15];
+    zernike15(rp * inv_radius, rp > 0.0 ? dx / rp : 1.0, rp > 0.0 ? dy / rp : 0.0, z);
+    double phi = 0.0;
+    for (int j = 0; j < p.ncoeffs; ++j) phi += p.c[j] * z[j];
+    turns += fmod(phi / 3.14159265358979323846, 2.0);
+    double sn, cs;
+    sincospi(turns, &sn, &cs);
+    p.cp[i] = make_float2((float)cs, (float)sn);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pupil_table(const Plan& pl, cudaStream_t s) {
+  PupilParams p;
+  p.cp = (float2*)(pl.ws + pl.off_cp);
+  p.nx = pl.nx;
+  p.ny = pl.ny;
+  p.ncoeffs = pl.sh_ncoeffs;
+  p.alpha = pl.sh_alpha;
+  for (int j = 0; j < 15; ++j) p.c[j] = j < pl.sh_ncoeffs ? pl.sh_coeffs[j] : 0.0;
+  pupil_table_kernel<<<2 * pl.num_sms, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 bool generic_lateral_supported(int nx, int ny) {
   auto ok = [](int n) {
     return n == 64 || n == 128 || n == 256 || n == 384 || n == 512 || n == 640 || n == 768 || n == 1024;

@@ -151,8 +151,10 @@ struct Plan {
   std::vector<float2> cx, cy, ox, oy, twx, twy, twl;
   std::vector<unsigned short> tcb;  // SSOCT_FLAG_TC_AXIAL: BF16 hi / lo 16-point DFT matrix (operand layout)
   // SSOCT_FLAG_PUPIL: input chirp x Zernike screen, its distance z and |K|, frames per Q chunk
-  std::vector<float2> cp;
   double sh_z = 0.0, sh_alpha = 0.0;
+  double sh_coeffs[15] = {};
+  int sh_ncoeffs = 0;
+  bool sh_dirty = false;     // the device table is built by the next ssoct_sharpness
   int sh_tpc = 8;
   bool sh_ready = false;
   // geometry of the device work
@@ -217,6 +219,7 @@ bool generic_lateral_supported(int nx, int ny);
 cudaError_t launch_lateral_generic(const Plan& pl, const uint16_t* frames, int ring_start, cudaStream_t s);
 void build_pupil_table(int nx, int ny, double alpha, const double* coeffs, int ncoeffs, std::vector<float2>& out);
 cudaError_t launch_sharpness(const Plan& pl, const uint16_t* frames, float* vol, cudaStream_t s);
+cudaError_t launch_pupil_table(const Plan& pl, cudaStream_t s);
 // Dynamic shared memory of the lateral kernel for a plan (bytes).
 size_t lateral_smem_bytes(const Plan& p);
 // Columns per column item of the lateral kernel for a column length ny.

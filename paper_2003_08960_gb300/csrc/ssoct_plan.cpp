@@ -640,10 +640,10 @@ ssoct_status ssoct_set_pupil(ssoct_plan h, const double* coeffs, int ncoeffs, do
   if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
   p.sh_z = z_m;
   p.sh_alpha = p.pitch * p.pitch / (p.lambda1 * z_m);
-  build_pupil_table(p.nx, p.ny, p.sh_alpha, coeffs, ncoeffs, p.cp);
-  cudaError_t e = cudaMemcpy(p.ws + p.off_cp, p.cp.data(), sizeof(float2) * p.cp.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(&p, e, "pupil table upload");
+  p.sh_ncoeffs = ncoeffs;
+  for (int j = 0; j < 15; ++j) p.sh_coeffs[j] = j < ncoeffs ? coeffs[j] : 0.0;
   p.sh_ready = true;
+  p.sh_dirty = true;
   return SSOCT_OK;
 }
 
@@ -657,7 +657,13 @@ ssoct_status ssoct_sharpness(ssoct_plan h, const uint16_t* frames_dev, float* vo
     return fail(&p, SSOCT_EINVAL, "frames, volume (16-byte aligned) and output must be non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
   p.lat_upto = -1;  // the intermediate no longer holds sliding-gate holograms
-  cudaError_t e = launch_sharpness(p, frames_dev, vol_dev, s);
+  cudaError_t e = cudaSuccess;
+  if (p.sh_dirty) {
+    e = launch_pupil_table(p, s);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "pupil table kernel");
+    p.sh_dirty = false;
+  }
+  e = launch_sharpness(p, frames_dev, vol_dev, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "sharpness kernels");
   e = cudaMemcpyAsync(out_host, p.ws + p.off_red + 2 * sizeof(double), 17 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "loss and gradient read-back");

@@ -42,7 +42,7 @@ def test_batch_equals_separate_reconstructs(ss):
     frames = [_dev(w.frames) for w in ws]
     refs = [p.reconstruct(f) for p, f in zip(plans, frames)]
     torch.cuda.synchronize()
-    batch = ss.Batch(plans)
+    batch = ss.Batch(plans, lanes=0)
     vols = [p.empty_volume()[0] for p in plans]
     for _ in range(3):
         for v in vols:
