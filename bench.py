@@ -184,7 +184,7 @@ def run_ssoct(args):
         w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=3 + rank)
     else:
         w = synth.workload(WORKLOAD, seed=3 + rank)
-    flags = ss.SSOCT_FLAG_TC_AXIAL if args.tc_axial else 0
+    flags = (ss.SSOCT_FLAG_TC_AXIAL if args.tc_axial else 0) | (ss.SSOCT_FLAG_AXIAL_FIRST if args.axial_first else 0)
     plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=flags)
     h = plan.handle
     stream = torch.cuda.Stream()
@@ -252,8 +252,16 @@ def run_ssoct(args):
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
     e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
-    lat_bytes = w.nx * w.ny * nl * 2 + voxels * 8
-    ax_bytes = voxels * (8 + 4)
+    if args.axial_first:
+        # rescale-axial pass: uint16 frames in, half-spectrum planes out; lateral
+        # pass: the planes in (each read once from HBM, its conjugate use from L2),
+        # |V|^2 out
+        plane_bytes = w.nx * w.ny * (nl // 2 + 1) * 8
+        ax_bytes = w.nx * w.ny * nl * 2 + plane_bytes
+        lat_bytes = plane_bytes + voxels * 4
+    else:
+        lat_bytes = w.nx * w.ny * nl * 2 + voxels * 8
+        ax_bytes = voxels * (8 + 4)
     kernels = {
         "lateral": {"ms": lat_ms, "bytes": lat_bytes, "GBps": lat_bytes / (lat_ms * 1e-3) / 1e9},
         "axial": {"ms": ax_ms, "bytes": ax_bytes, "GBps": ax_bytes / (ax_ms * 1e-3) / 1e9},
@@ -273,7 +281,8 @@ def run_ssoct(args):
                    "window": [0, 0, wx, wy],
                    "schedule": ({k: tune[k] for k in ("lag", "ring_slots", "tc_axial")} if tune
                                 else "plan default (lag 2, 6 ring slots)"),
-                   "form": "tensor-core axial (bf16 hi+lo, fp32 accumulate)" if tc_main else "fp32 (paper order)",
+                   "form": ("fp32, axial-first order (Eq. 5 + Eq. 7, then Eq. 6 per depth bin)" if args.axial_first
+                            else "tensor-core axial (bf16 hi+lo, fp32 accumulate)" if tc_main else "fp32 (paper order)"),
                    "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["GBps"], "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
@@ -549,6 +558,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default schedule")
+    ap.add_argument("--axial-first", action="store_true",
+                    help="Eq. 5 + Eq. 7 before Eq. 6 (SSOCT_FLAG_AXIAL_FIRST) for the main line")
     ap.add_argument("--tc-axial", action="store_true", help="time the tensor-core axial form as the main line "
                                                             "(profiling captures)")
     ap.add_argument("--size", default=None, help="NXxNYxNLAMBDA instead of the 1024x1024x256 workload "

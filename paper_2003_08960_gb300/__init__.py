@@ -21,7 +21,7 @@ import numpy as np
 from . import _abi
 from ._abi import (  # noqa: F401
     SSOCT_EDROPPED, SSOCT_EINVAL, SSOCT_ENOMEM, SSOCT_ENOTREADY, SSOCT_EUNSUPPORTED, SSOCT_ETIMEOUT,
-    SSOCT_FLAG_MAGNITUDE, SSOCT_FLAG_PUPIL, SSOCT_FLAG_TC_AXIAL, SSOCT_OK, ssoct_plan_info_t, ssoct_window,
+    SSOCT_FLAG_AXIAL_FIRST, SSOCT_FLAG_MAGNITUDE, SSOCT_FLAG_PUPIL, SSOCT_FLAG_TC_AXIAL, SSOCT_OK, ssoct_plan_info_t, ssoct_window,
 )
 
 

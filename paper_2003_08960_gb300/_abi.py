@@ -25,6 +25,7 @@ SSOCT_EUNSUPPORTED = 8
 SSOCT_FLAG_MAGNITUDE = 0x1
 SSOCT_FLAG_TC_AXIAL = 0x2
 SSOCT_FLAG_PUPIL = 0x4
+SSOCT_FLAG_AXIAL_FIRST = 0x8
 
 STATUS_NAMES = {
     0: "SSOCT_OK", 1: "SSOCT_EINVAL", 2: "SSOCT_ENOMEM", 3: "SSOCT_ECUDA", 4: "SSOCT_EAGAIN",

@@ -27,8 +27,8 @@ std::string tune_key(const Plan& p) {
   for (char& c : name)
     if (c == '"' || c == '\\') c = '_';
   char buf[256];
-  snprintf(buf, sizeof buf, "%s|%d|%dx%dx%d|%d,%d,%d,%d", name.c_str(), p.num_sms, p.nx, p.ny, p.nl, p.x0, p.y0,
-           p.wx, p.wy);
+  snprintf(buf, sizeof buf, "%s|%d|%dx%dx%d|%d,%d,%d,%d%s", name.c_str(), p.num_sms, p.nx, p.ny, p.nl, p.x0, p.y0,
+           p.wx, p.wy, p.axial_first ? "|axial-first" : "");
   return buf;
 }
 
@@ -122,7 +122,7 @@ extern "C" ssoct_status ssoct_autotune(ssoct_plan h, const uint16_t* frames_dev,
   // times the axial forms this sweep length has.
   std::vector<Choice> cand;
   const int lags[] = {1, 2, 3};
-  for (int tc = 0; tc <= (axial_tc_supported(p.nl) ? 1 : 0); ++tc) {
+  for (int tc = 0; tc <= (axial_tc_supported(p.nl) && !p.axial_first ? 1 : 0); ++tc) {
     if (p.generic) {
       cand.push_back(Choice{initial.lag, initial.slots, tc});
       continue;

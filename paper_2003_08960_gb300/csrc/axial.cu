@@ -62,6 +62,73 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_kernel(const __gr
   });
 }
 
+struct RescaleAxialParams {
+  const uint16_t* frames;  // gate frame t at frames[(ring_start + t) mod nl]
+  int ring_start;
+  const Tap* xtab;         // [nl][nx]
+  const Tap* ytab;         // [nl][ny]
+  const float2* twl;       // [N2l][N1l], sign -
+  float2* planes;          // [nl/2 + 1][ny][nx]
+  int nx, ny, nl;
+};
+
+// Axial-first order, first pass: at every sensor pixel of a 32-pixel tile, the
+// Eq. 5 resample of each frame of the gate (a real series over t), its Eq. 7
+// transform over t, and bins q = 0 .. nl/2 as complex planes.  The rest of the
+// spectrum is the conjugate mirror (real input) and is formed by the lateral
+// pass.  Eq. 6 is linear and the same for every frame, so transforming over t
+// before it gives the same V as the paper's order.
+template <int NL>
+__global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(const __grid_constant__ RescaleAxialParams p) {
+  constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  static_assert(N2 % N1 == 0, "the second stage needs N1 | N2");
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* ex = reinterpret_cast<float2*>(smem);
+  const int pix = threadIdx.x % kTile, j1 = threadIdx.x / kTile;
+  const int x = blockIdx.x * kTile + pix, y = blockIdx.y;
+  float2 a[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) {
+    const int t = j1 + N1 * j2;
+    const uint16_t* fr = p.frames + (size_t)((p.ring_start + t) % p.nl) * p.ny * p.nx;
+    const float u = rescale_tap_value(fr, p.nx, p.xtab[(size_t)t * p.nx + x], p.ytab[(size_t)t * p.ny + y]);
+    a[j2] = make_float2(u, 0.f);
+  }
+  Dft<N2, -1>::template run<1, 0>(a);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(p.twl + k2 * N1 + j1));
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * kTile + pix] = a[k2];
+  __syncthreads();
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * kTile + pix];
+    Dft<N1, -1>::template run<1, i * N1>(a);
+  });
+  const size_t plane = (size_t)p.ny * p.nx;
+  float2* dst = p.planes + (size_t)y * p.nx + x;
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const int q = k2 + N2 * k1;
+      if (q <= NL / 2) dst[(size_t)q * plane] = a[i * N1 + k1];
+    }
+  });
+}
+
+template <int NL>
+cudaError_t launch_ra(const RescaleAxialParams& rp, cudaStream_t s) {
+  const size_t smem = (size_t)NL * kTile * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(rescale_axial_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  rescale_axial_kernel<NL><<<dim3(rp.nx / kTile, rp.ny), kTile * Split<NL>::N1, smem, s>>>(rp);
+  return cudaGetLastError();
+}
+
 template <int NL>
 cudaError_t launch(const AxialParams& ap, cudaStream_t s) {
   const size_t smem = (size_t)NL * kTile * sizeof(float2);
@@ -75,6 +142,24 @@ cudaError_t launch(const AxialParams& ap, cudaStream_t s) {
 #define SSOCT_AXIAL_SIZES(X) X(16) X(32) X(64) X(96) X(128) X(160) X(200) X(256) X(512)
 
 }  // namespace
+
+cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring_start, float2* planes,
+                                 cudaStream_t s) {
+  RescaleAxialParams rp;
+  rp.frames = frames;
+  rp.ring_start = ring_start;
+  rp.xtab = (const Tap*)(p.ws + p.off_xtab);
+  rp.ytab = (const Tap*)(p.ws + p.off_ytab);
+  rp.twl = (const float2*)(p.ws + p.off_twl);
+  rp.planes = planes;
+  rp.nx = p.nx;
+  rp.ny = p.ny;
+  rp.nl = p.nl;
+#define X(a) if (p.nl == a) return launch_ra<a>(rp, s);
+  SSOCT_AXIAL_SIZES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
 
 bool axial_supported(int nl) {
 #define X(a) if (nl == a) return true;

@@ -96,4 +96,14 @@ __device__ __forceinline__ float u16hi_to_f(unsigned w) {
   return __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5432)) - 8388608.0f;
 }
 
+// Eq. 5 at one pixel of a uint16 frame [.][nx] from its separable taps (weights
+// are 0 where a tap falls outside the frame; bases are clamped inside it).
+__device__ __forceinline__ float rescale_tap_value(const uint16_t* fr, int nx, const Tap& tx, const Tap& ty) {
+  const uint16_t* r0 = fr + (size_t)ty.base * nx + tx.base;
+  const uint16_t* r1 = r0 + nx;
+  const float v0 = fmaf(tx.w0, (float)__ldg(r0), tx.w1 * (float)__ldg(r0 + 1));
+  const float v1 = fmaf(tx.w0, (float)__ldg(r1), tx.w1 * (float)__ldg(r1 + 1));
+  return fmaf(ty.w0, v0, ty.w1 * v1);
+}
+
 }  // namespace ssoct

@@ -40,6 +40,15 @@ struct Desc {
   int kind, f, item, jlo, nrows, slot;  // slot: wavelength / intermediate index of frame f
 };
 
+// Axial-first order: frame f of the lateral pass is depth bin af_bin(f), in the
+// order 0, 1, N-1, 2, N-2, ..., N/2, so that the two bins sharing a half-spectrum
+// plane (q and N - q) follow each other and the second read of the plane hits L2.
+__host__ __device__ __forceinline__ int af_bin(int f, int nl) {
+  if (f == 0) return 0;
+  const int k = (f + 1) / 2;
+  return (f & 1) ? k : nl - k;
+}
+
 // ---------------------------------------------------------------- mbarrier / TMA
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -183,7 +192,7 @@ __device__ __forceinline__ float u16_to_f(unsigned short u) {
 // Row item: rows [item*RPI, item*RPI + RPI) of frame d.f.  The stage buffer holds
 // input rows jlo .. jlo + nrows - 1 (uint16) and the taps; it then serves as the
 // transpose block and, for whole-frame plans, as the output [RPI][NX].
-template <int NX, int NY, bool FW>
+template <int NX, int NY, bool FW, bool AF>
 __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, unsigned char* buf,
                                          const float2* twx, const float2* cxs) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
@@ -198,9 +207,23 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   const Tap* ytaps = xtaps + NX;
   const float2* ychirp = reinterpret_cast<const float2*>(ytaps + RPI);
   // 1. Eq. 5 resample (taps outside the frame carry weight 0) x input chirp,
-  //    elements n = j1 + N1 * j2 of row y
+  //    elements n = j1 + N1 * j2 of row y; in axial-first order the row of the
+  //    half-spectrum plane of bin q (conjugated for q > N/2) x input chirp
   float2 a[N2];
-  {
+  float2 cyv;
+  if constexpr (AF) {
+    const float2* in2 = reinterpret_cast<const float2*>(buf) + r * NX;
+    const bool cj = af_bin(f, p.nl) > p.nl / 2;
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) {
+      const int n = j1 + N1 * j2;
+      float2 v = in2[n];
+      if (cj) v.y = -v.y;
+      a[j2] = cmul(v, cxs[n]);
+    }
+    cyv = ldg2(p.cy + y);
+  } else {
+    cyv = ychirp[r];
     const Tap ty = ytaps[r];
     const uint16_t* r0 = in + (ty.base - d.jlo) * NX;
     const uint16_t* r1 = r0 + NX;
@@ -218,11 +241,8 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   // 2. row DFT (+ sign of Eq. 6): N2-point DFT in registers, twiddle with the
   //    row's y chirp folded in, transpose in the stage buffer, N1-point DFTs
   Dft<N2, 1>::template run<1, 0>(a);
-  {
-    const float2 cyv = ychirp[r];
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
-  }
+  for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
   consumers_sync();  // every input of the buffer has been read
   float2* ex = reinterpret_cast<float2*>(buf) + r * NX;  // this row's block (N2 x N1 = NX values)
 #pragma unroll
@@ -270,7 +290,7 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
 // buffer holds the band [NY][BC] copied from the scratch slot; both DFT passes
 // work in place, and whole-frame plans leave the output [NY][BC] there for the
 // producer's tensor store.
-template <int NY, bool FW>
+template <int NY, bool FW, bool AF>
 __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, unsigned char* buf,
                                          const float2* twy) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
@@ -295,7 +315,33 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = tile[(jj + N1 * k2) * BC + b];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  if constexpr (FW && kTmaOut) {
+  if constexpr (AF) {
+    // axial-first order: the column DFT completes V of bin q; write |V|^2 |K|^2
+    // (or |V| |K|) and optionally V with the output chirp and K
+    const int kxw = d.item * BC + b;  // column bands already span the window's columns
+    if (kxw < p.wx) {
+      const int q = af_bin(d.f, p.nl);
+      float* vdst = p.vol + (size_t)q * p.wy * p.wx + kxw;
+      float2 ox = make_float2(0.f, 0.f);
+      if (p.cplx) ox = ldg2(p.ox + kxw);
+      static_for<0, N2 / N1>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const int k2 = j1 + N1 * i;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const int kyw = k2 + N2 * k1 - (FW ? 0 : p.y0);
+          if (FW || (kyw >= 0 && kyw < p.wy)) {
+            const float2 v = a[i * N1 + k1];
+            float pw = fmaf(v.x, v.x, v.y * v.y) * p.power_scale;
+            if (p.magnitude) pw = sqrtf(pw);
+            __stcs(vdst + (size_t)kyw * p.wx, pw);
+            if (p.cplx)
+              __stcs(p.cplx + ((size_t)q * p.wy + kyw) * p.wx + kxw, cmul(v, cmul(ox, ldg2(p.oy + kyw))));
+          }
+        }
+      });
+    }
+  } else if constexpr (FW && kTmaOut) {
     consumers_sync();  // every transposed read is done
     static_for<0, N2 / N1>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -336,7 +382,7 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
 // are in global memory: right after done[b] when the consumers stored them,
 // after the TMA writes complete otherwise.  Every wait keeps servicing finished
 // items, so a CTA never holds back a completion another CTA is waiting for.
-template <int NX, int NY, bool FW>
+template <int NX, int NY, bool FW, bool AF>
 __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const CUtensorMap* tmap_inter,
                          uint64_t* full_bar, uint64_t* done_bar, Desc* desc, unsigned char* stage0) {
   constexpr int RPI = kThreads / Split<NX>::N1;
@@ -480,7 +526,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
     fence_proxy_async_global();  // the acquired data is read by TMA (async proxy)
     const int slot = (p.tab0 + f) % p.nl;
     Desc d{kind, f, item, 0, 0, slot};
-    if (kind == kRowItem) {
+    if (kind == kRowItem && !AF) {
       const Tap* yt = p.ytab + (size_t)slot * NY;
       d.jlo = yt[item * RPI].base;
       d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
@@ -507,7 +553,14 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       break;
     }
     desc[b] = d;
-    if (kind == kRowItem) {
+    if (AF && kind == kRowItem) {
+      // RPI contiguous rows of the half-spectrum plane of bin af_bin(f)
+      const int q = af_bin(f, p.nl);
+      const int plane = q <= p.nl / 2 ? q : p.nl - q;
+      const unsigned bytes = (unsigned)(RPI * NX * sizeof(float2));
+      mbar_arrive_tx(&full_bar[b], bytes);
+      tma_load_1d(buf, p.aplanes + ((size_t)plane * NY + item * RPI) * NX, bytes, &full_bar[b]);
+    } else if (kind == kRowItem) {
       const unsigned bytes = (unsigned)(d.nrows * NX * sizeof(uint16_t));
       const unsigned tap_off = (unsigned)row_taps_offset<NX>(d.nrows);
       const unsigned tap_bytes = (unsigned)(NX * sizeof(Tap));
@@ -553,7 +606,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
   flush();
 }
 
-template <int NX, int NY, bool FW>
+template <int NX, int NY, bool FW, bool AF>
 __global__ void __launch_bounds__(kCtaThreads, 1)
     lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap,
                    const __grid_constant__ CUtensorMap tmap_inter) {
@@ -579,7 +632,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   float2* twy = twx + NX;
   float2* cxs = twy + NY;
   if (tid >= kThreads) {
-    if (tid == kThreads) producer<NX, NY, FW>(p, &tmap, &tmap_inter, full_bar, done_bar, desc, stage0);
+    if (tid == kThreads) producer<NX, NY, FW, AF>(p, &tmap, &tmap_inter, full_bar, done_bar, desc, stage0);
     return;
   }
   for (int i = tid; i < NX; i += kThreads) {
@@ -600,9 +653,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     if (d.kind == kEndItem) break;
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     if (d.kind == kRowItem)
-      row_item<NX, NY, FW>(p, d, buf, twx, cxs);
+      row_item<NX, NY, FW, AF>(p, d, buf, twx, cxs);
     else
-      col_item<NY, FW>(p, d, buf, twy);
+      col_item<NY, FW, AF>(p, d, buf, twy);
     mbar_arrive(&done_bar[b]);
     if (++b == kStages) {
       b = 0;
@@ -634,33 +687,36 @@ size_t smem_for(const Plan& p) {
   return total;
 }
 
-template <int NX, int NY, bool FW>
+template <int NX, int NY, bool FW, bool AF>
 cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, const void* tmap, const void* tmap_inter,
                       int num_sms, cudaStream_t s) {
   size_t sb, smem;
   smem_layout<NX, NY>(p, sb, smem);
   LateralParams lp = lp_in;
   lp.stage_bytes = (int)sb;
-  cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(lateral_kernel<NX, NY, FW, AF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const long long total = lp.sch.total();
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY, FW>, kCtaThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lateral_kernel<NX, NY, FW, AF>, kCtaThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = (num_sms > 0 ? num_sms : 1) * per_sm;
   if (grid > total) grid = (int)total;
-  lateral_kernel<NX, NY, FW><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(tmap),
-                                                             *reinterpret_cast<const CUtensorMap*>(tmap_inter));
+  lateral_kernel<NX, NY, FW, AF><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(tmap),
+                                                                 *reinterpret_cast<const CUtensorMap*>(tmap_inter));
   return cudaGetLastError();
 }
 
 template <int NX, int NY>
 cudaError_t launch(const Plan& p, const LateralParams& lp, const void* tmap, const void* tmap_inter, int num_sms,
                    cudaStream_t s) {
-  return lateral_full_window(p) ? launch_fw<NX, NY, true>(p, lp, tmap, tmap_inter, num_sms, s)
-                                : launch_fw<NX, NY, false>(p, lp, tmap, tmap_inter, num_sms, s);
+  if (p.axial_first)
+    return lateral_full_window(p) ? launch_fw<NX, NY, true, true>(p, lp, tmap, tmap_inter, num_sms, s)
+                                  : launch_fw<NX, NY, false, true>(p, lp, tmap, tmap_inter, num_sms, s);
+  return lateral_full_window(p) ? launch_fw<NX, NY, true, false>(p, lp, tmap, tmap_inter, num_sms, s)
+                                : launch_fw<NX, NY, false, false>(p, lp, tmap, tmap_inter, num_sms, s);
 }
 
 #define SSOCT_LATERAL_SIZES(X) \

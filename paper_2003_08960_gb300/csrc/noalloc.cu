@@ -47,6 +47,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
                                                          void* complex_dev, void* stream) {
   if (!h) return SSOCT_EINVAL;
   Plan& p = plan_of(h);
+  if (p.axial_first) return fail(p, SSOCT_EUNSUPPORTED, "the no-allocation entry point runs the paper's order");
   if (p.generic) return fail(p, SSOCT_EUNSUPPORTED, "the no-allocation entry point needs a frame size of the persistent lateral kernel");
   if (p.ws_bytes > kNoAllocBytes) {
     char msg[200];

@@ -44,16 +44,6 @@ struct Lat {
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-__device__ __forceinline__ float u16_to_float(const uint16_t* p) { return (float)__ldg(p); }
-
-// Eq. 5 at (x, y) of frame `fr` from separable taps (weights 0 outside the frame).
-__device__ __forceinline__ float resample(const uint16_t* fr, int nx, const Tap& tx, const Tap& ty) {
-  const uint16_t* r0 = fr + (size_t)ty.base * nx + tx.base;
-  const uint16_t* r1 = r0 + nx;
-  const float v0 = fmaf(tx.w0, u16_to_float(r0), tx.w1 * u16_to_float(r0 + 1));
-  const float v1 = fmaf(tx.w0, u16_to_float(r1), tx.w1 * u16_to_float(r1 + 1));
-  return fmaf(ty.w0, v0, ty.w1 * v1);
-}
 
 // Row DFT of sign S over the registers of thread (r, j1) of an N1 x N2 split:
 // on entry a[j2] = x[j1 + N1 j2]; on exit a[i N1 + k1] = X[k2 + N2 k1] with
@@ -145,7 +135,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_fwd_kernel(const __grid_cons
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) {
     const int n = j1 + N1 * j2;
-    const float u = resample(fr, NX, p.xtab[(size_t)t * NX + n], ty);
+    const float u = rescale_tap_value(fr, NX, p.xtab[(size_t)t * NX + n], ty);
     const float2 c = ldg2(cp + n);
     a[j2] = make_float2(u * c.x, u * c.y);
   }
@@ -314,7 +304,7 @@ __global__ void __launch_bounds__(kRowThreads) rows_adj_kernel(const __grid_cons
       if (N2 % N1 == 0 || k2 < N2) {
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
-          const float u = resample(fr, NX, xt[k2 + N2 * k1], ty);
+          const float u = rescale_tap_value(fr, NX, xt[k2 + N2 * k1], ty);
           const float2 v = a[i * N1 + k1];
           acc[i * N1 + k1].x = fmaf(v.x, u, acc[i * N1 + k1].x);   // conj(Y) u
           acc[i * N1 + k1].y = fmaf(-v.y, u, acc[i * N1 + k1].y);

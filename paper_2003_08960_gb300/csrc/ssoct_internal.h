@@ -115,6 +115,15 @@ struct LateralParams {
   int stage_rows;          // input rows staged per row item (max over items)
   int stage_bytes;         // bytes of one shared-memory stage buffer (set at launch)
   unsigned long long wait_ns;  // limit of every device-side wait (0 = default)
+  // axial-first order (SSOCT_FLAG_AXIAL_FIRST): frame f is depth bin af_bin(f);
+  // row items read half-spectrum planes, column items write the volume
+  const float2* aplanes;   // [nl/2 + 1][ny][nx]
+  float* vol;              // [nl][wy][wx]
+  float2* cplx;            // optional [nl][wy][wx]
+  const float2* ox;        // [wx] output chirp (x)
+  const float2* oy;        // [wy] output chirp (y) times K
+  float power_scale;       // |K|^2
+  int magnitude;
 };
 
 struct AxialParams {
@@ -173,6 +182,10 @@ struct Plan {
   // take the two-pass lateral path of sharpness.cu: chirp table and frame buffer.
   bool generic = false;
   size_t off_cg = 0;
+  // SSOCT_FLAG_AXIAL_FIRST: Eq. 5 + Eq. 7 first (half spectrum of the real
+  // rescaled frames), then the lateral kernel on the planes
+  bool axial_first = false;
+  size_t off_aplanes = 0;
   char* ws = nullptr;
   int device = -1;
   int num_sms = 0;
@@ -198,6 +211,10 @@ struct Plan {
 cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s);
 cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s);
 cudaError_t launch_cuts(const CutsParams& cp, cudaStream_t s);
+// Axial-first order, first pass: Eq. 5 resample of every frame and Eq. 7 over
+// the sweep at every pixel, bins 0..nl/2 written as planes [nl/2 + 1][ny][nx].
+cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring_start, float2* planes,
+                                 cudaStream_t s);
 bool lateral_supported(int nx, int ny);
 bool axial_supported(int nl);
 // Tensor-core axial kernel (axial_tc.cu): sweep lengths it handles, its DFT

@@ -199,13 +199,15 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
     return SSOCT_EINVAL;
   for (int t = 0; t < nlambda; ++t)
     if (!(lambda_m[t] > 0.0) || !std::isfinite(lambda_m[t])) return SSOCT_EINVAL;
-  if (flags & ~(SSOCT_FLAG_MAGNITUDE | SSOCT_FLAG_TC_AXIAL | SSOCT_FLAG_PUPIL)) return SSOCT_EINVAL;
+  if (flags & ~(SSOCT_FLAG_MAGNITUDE | SSOCT_FLAG_TC_AXIAL | SSOCT_FLAG_PUPIL | SSOCT_FLAG_AXIAL_FIRST)) return SSOCT_EINVAL;
   ssoct_window w = win ? *win : ssoct_window{0, 0, nx, ny};
   if (w.x0 < 0 || w.y0 < 0 || w.wx < 1 || w.wy < 1 || w.x0 + w.wx > nx || w.y0 + w.wy > ny)
     return SSOCT_EINVAL;
   if (!axial_supported(nlambda)) return SSOCT_EUNSUPPORTED;
   const bool generic = !lateral_supported(nx, ny);  // two-pass lateral path for the other sizes
   if (generic && !generic_lateral_supported(nx, ny)) return SSOCT_EUNSUPPORTED;
+  if ((flags & SSOCT_FLAG_AXIAL_FIRST) && (generic || (nlambda & 1) || (flags & SSOCT_FLAG_TC_AXIAL)))
+    return SSOCT_EUNSUPPORTED;
   if ((flags & SSOCT_FLAG_TC_AXIAL) && !axial_tc_supported(nlambda)) return SSOCT_EUNSUPPORTED;
   if ((flags & SSOCT_FLAG_PUPIL) && !sharpness_supported(nx, ny, nlambda)) return SSOCT_EUNSUPPORTED;
 
@@ -216,6 +218,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.x0 = w.x0; p.y0 = w.y0; p.wx = w.wx; p.wy = w.wy;
   p.flags = flags;
   p.generic = generic;
+  p.axial_first = (flags & SSOCT_FLAG_AXIAL_FIRST) != 0;
   p.pitch = pitch_m; p.z = z_m;
   p.lambdas.assign(lambda_m, lambda_m + nlambda);
   p.lambda1 = lambda_m[0];
@@ -312,6 +315,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_scratch = take(generic ? 0 : sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
   p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
   if (generic) p.off_cg = take(sizeof(float2) * (size_t)nx * ny);
+  if (p.axial_first) p.off_aplanes = take(sizeof(float2) * (size_t)(nlambda / 2 + 1) * ny * nx);
   if (generic || (flags & SSOCT_FLAG_PUPIL)) p.off_F = take(sizeof(float2) * (size_t)nlambda * ny * nx);
   if (flags & SSOCT_FLAG_PUPIL) {
     const size_t chunks = (size_t)(nlambda + p.sh_tpc - 1) / p.sh_tpc;
@@ -498,8 +502,18 @@ static ssoct_status launch_lateral_pass(Plan& p, const LateralParams& lp, cudaSt
     p.events_used += 3;
     cudaEventRecord((*ev)[0], s);
   }
+  if (p.axial_first) {
+    // Eq. 5 + Eq. 7 first: the interval between events 0 and 1 is this pass
+    e = launch_rescale_axial(p, lp.frames, lp.ring_start, (float2*)(ws + p.off_aplanes), s);
+    if (e != cudaSuccess) return cuda_fail(&p, e, "rescale-axial kernel launch");
+    if (*ev) cudaEventRecord((*ev)[1], s);
+  }
   e = p.generic ? launch_lateral_generic(p, lp.frames, lp.ring_start, s) : launch_lateral(p, lp, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "lateral kernel launch");
+  if (p.axial_first) {
+    if (*ev) cudaEventRecord((*ev)[2], s);
+    return SSOCT_OK;
+  }
   if (*ev) cudaEventRecord((*ev)[1], s);
   return SSOCT_OK;
 }
@@ -529,11 +543,21 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
                                cudaStream_t s) {
   if (!vol || ((uintptr_t)vol % 16) || ((uintptr_t)cplx % 16))
     return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
-  const LateralParams lp = lateral_params(p, frames, ring_start, 0);
+  LateralParams lp = lateral_params(p, frames, ring_start, 0);
   p.lat_upto = -1;  // the intermediate no longer holds the sliding-gate holograms
+  if (p.axial_first) {
+    // the lateral pass writes the volume itself
+    lp.aplanes = (const float2*)(p.ws + p.off_aplanes);
+    lp.vol = vol;
+    lp.cplx = (float2*)cplx;
+    lp.ox = (const float2*)(p.ws + p.off_ox);
+    lp.oy = (const float2*)(p.ws + p.off_oy);
+    lp.power_scale = (float)(p.alpha * p.alpha);
+    lp.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
+  }
   cudaEvent_t* ev = nullptr;
   ssoct_status st = launch_lateral_pass(p, lp, s, &ev);
-  if (st != SSOCT_OK) return st;
+  if (st != SSOCT_OK || p.axial_first) return st;
   return launch_axial_pass(p, vol, cplx, s, ev);
 }
 
@@ -561,6 +585,7 @@ ssoct_status ssoct_reconstruct_sliding(ssoct_plan h, float* vol_dev, void* compl
   Plan& p = h->p;
   if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
   if (p.generic) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need a frame size of the persistent lateral kernel");
+  if (p.axial_first) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need the paper's order (no SSOCT_FLAG_AXIAL_FIRST)");
   if (p.stream_count < p.nl) return fail(&p, SSOCT_ENOTREADY, "fewer than nlambda frames pushed");
   if (!vol_dev || ((uintptr_t)vol_dev % 16) || ((uintptr_t)complex_dev % 16))
     return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
@@ -699,8 +724,9 @@ ssoct_status ssoct_profile_read(ssoct_plan h, double* lateral_ms, double* axial_
     if (e != cudaSuccess) return cuda_fail(&p, e, "event elapsed");
     e = cudaEventElapsedTime(&b, p.events[i + 1], p.events[i + 2]);
     if (e != cudaSuccess) return cuda_fail(&p, e, "event elapsed");
-    lat += a;
-    ax += b;
+    // axial-first plans record the rescale-axial pass first
+    lat += p.axial_first ? b : a;
+    ax += p.axial_first ? a : b;
   }
   if (lateral_ms) *lateral_ms = lat;
   if (axial_ms) *axial_ms = ax;

@@ -63,8 +63,18 @@ def test_create_plan_validation(ss):
     st, h = ss.ssoct_create_plan(64, 64, 24, 20e-6, 0.3, np.linspace(800e-9, 850e-9, 24))
     assert st == ss.SSOCT_EUNSUPPORTED
     # unknown flag bits; the tensor-core axial form exists for nlambda = 256 only
-    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=0x8)
+    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=0x10)
     assert st == ss.SSOCT_EINVAL
+    # axial-first order: persistent-kernel sizes, even sweeps, not with the tensor-core form
+    st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_AXIAL_FIRST)
+    assert st == ss.SSOCT_OK
+    ss.ssoct_destroy_plan(h)
+    st, h = ss.ssoct_create_plan(384, 384, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_AXIAL_FIRST)
+    assert st == ss.SSOCT_EUNSUPPORTED
+    lam256 = np.linspace(800e-9, 850e-9, 256)
+    st, h = ss.ssoct_create_plan(64, 64, 256, 20e-6, 0.3, lam256,
+                                 flags=ss.SSOCT_FLAG_AXIAL_FIRST | ss.SSOCT_FLAG_TC_AXIAL)
+    assert st == ss.SSOCT_EUNSUPPORTED
     st, h = ss.ssoct_create_plan(64, 64, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_TC_AXIAL)
     assert st == ss.SSOCT_EUNSUPPORTED and h is None
     lam256 = np.linspace(800e-9, 850e-9, 256)

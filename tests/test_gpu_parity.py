@@ -315,3 +315,50 @@ def test_mixed_radix_ring_path(ss):
     with pytest.raises(ss.SsoctError) as e:
         plan.reconstruct_sliding()
     assert e.value.status == ss.SSOCT_EUNSUPPORTED
+
+
+# Axial-first order (SSOCT_FLAG_AXIAL_FIRST): Eq. 5 and Eq. 7 first, then Eq. 6
+# per depth bin writing the volume; the same V as the paper's order.
+@pytest.mark.parametrize("shape,window", [((64, 64, 32), None), ((64, 64, 32), (36, 40, 23, 17)),
+                                          ((128, 64, 16), None), ((64, 128, 64), (10, 20, 40, 90)),
+                                          ((128, 128, 128), None), ((256, 256, 256), None)])
+def test_axial_first_matches_oracle(ss, shape, window):
+    nx, ny, nl = shape
+    w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=nx + 2 * ny + nl)
+    plan, vol, cplx, ref = _run(ss, w, window=window, method="fft", flags=ss.SSOCT_FLAG_AXIAL_FIRST)
+    err = _check(vol, cplx, ref, quadrant=window is None)
+    print(f"axial-first {shape} window={window}: complex rel L2 {err:.3e}")
+
+
+def test_axial_first_ring_magnitude_profile(ss):
+    w = synth.workload("mid_512x512x128")
+    af = ss.SSOCT_FLAG_AXIAL_FIRST
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=af)
+    mag = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=af | ss.SSOCT_FLAG_MAGNITUDE)
+    paper = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    f = _dev(w.frames)
+    assert ss.ssoct_profile(plan.handle, True) == 0
+    v = plan.reconstruct(f)
+    st, lat, ax, calls = ss.ssoct_profile_read(plan.handle)
+    assert st == 0 and calls == 1 and lat > 0 and ax > 0
+    ss.ssoct_profile(plan.handle, False)
+    plan.push(_dev(w.frames[:30]), first_seq=0)
+    plan.push(f, first_seq=30)                     # the ring wraps: gate from slot 30
+    v_ring = plan.reconstruct_ring()
+    m = mag.reconstruct(f)
+    p = paper.reconstruct(f)
+    torch.cuda.synchronize()
+    assert torch.equal(v_ring, v)
+    assert torch.allclose(m * m, v, rtol=1e-5, atol=0)
+    assert float((v.double() - p.double()).norm() / p.double().norm()) <= 2e-6
+    with pytest.raises(ss.SsoctError) as e:
+        plan.reconstruct_sliding()
+    assert e.value.status == ss.SSOCT_EUNSUPPORTED
+
+
+@pytest.mark.slow
+def test_axial_first_paper_size_1024x1024x256(ss):
+    w = synth.workload("paper_1024x1024x256")
+    plan, vol, cplx, ref = _run(ss, w, method="fft", flags=ss.SSOCT_FLAG_AXIAL_FIRST)
+    err = _check(vol, cplx, ref)
+    print(f"axial-first 1024x1024x256 complex rel L2 = {err:.3e}")
