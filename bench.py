@@ -364,10 +364,33 @@ def _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world):
     for pl in plans:
         if ss.ssoct_sync(pl.handle, 0):
             raise RuntimeError("kernel error: " + ss.ssoct_last_error(pl.handle))
+    # the link's floor for the same bytes: the same H2D and D2H copies, with no
+    # kernels, on the same two streams
+    dev_frames = torch.empty(host_frames.shape, dtype=host_frames.dtype, device="cuda")
+
+    def copy_step(i):
+        with torch.cuda.stream(s_h2d):
+            dev_frames.copy_(host_frames, non_blocking=True)
+        with torch.cuda.stream(s_d2h):
+            host_vols[i].copy_(vols[i], non_blocking=True)
+
+    for k in range(2):
+        copy_step(k % 2)
+    torch.cuda.synchronize()
+    e0.record(s_h2d)
+    s_d2h.wait_event(e0)
+    for k in range(e2e_steps):
+        copy_step(k % 2)
+    s_h2d.wait_stream(s_d2h)
+    e1.record(s_h2d)
+    torch.cuda.synchronize()
+    copy_ms = e0.elapsed_time(e1) / e2e_steps
     e2e_ms, e2e_value = aggregate(e2e_ms, voxels, world, dist if world > 1 else None, device="cuda")
     return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_frames.numel() * 2),
             "d2h_bytes_per_step": int(host_vols[0].numel() * 4), "ms_per_step": e2e_ms,
-            "pipeline": "2 rings, H2D / reconstruct / D2H on 3 streams"}
+            "copy_floor_ms": copy_ms, "frac_of_copy_floor": copy_ms / e2e_ms,
+            "pipeline": "2 rings, H2D / reconstruct / D2H on 3 streams; copy floor = the same copies "
+                        "alone on the same streams (pinned host memory, host link bound)"}
 
 
 def _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream, step_frames=13):
@@ -408,8 +431,35 @@ def _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream, step_frames
     if ss.ssoct_sync(h, sp):
         raise RuntimeError("kernel error: " + ss.ssoct_last_error(h))
     ms = e0.elapsed_time(e1) / steps
+    # display mode: the same gate updates, only the three cuts of each gate
+    nl_, wy, wx = plan.volume_shape()
+    xy = torch.empty((wy, wx), dtype=torch.float32, device="cuda")
+    xz = torch.empty((nl_, wx), dtype=torch.float32, device="cuda")
+    yz = torch.empty((nl_, wy), dtype=torch.float32, device="cuda")
+    cut = (wx // 2 + wx // 4, wy // 2 + wy // 4, nl_ // 2)
+
+    def cuts_step():
+        nonlocal pos
+        push(step_frames, pos)
+        pos += step_frames
+        if ss.ssoct_sliding_cuts(h, cut[0], cut[1], cut[2], xy.data_ptr(), xz.data_ptr(), yz.data_ptr(), sp):
+            raise RuntimeError(ss.ssoct_last_error(h))
+
+    for _ in range(3):
+        cuts_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        cuts_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ss.ssoct_sync(h, sp):
+        raise RuntimeError("kernel error: " + ss.ssoct_last_error(h))
+    ms_cuts = e0.elapsed_time(e1) / steps
     return {"step_frames": step_frames, "ms_per_volume": ms, "volumes_per_s": 1000.0 / ms,
             "Gvoxel_per_s": voxels / (ms * 1e-3) / 1e9,
+            "cuts_only": {"ms_per_gate": ms_cuts, "gates_per_s": 1000.0 / ms_cuts,
+                          "note": "ssoct_sliding_cuts: xy, xz, yz of each gate, no volume"},
             "paper": "38 volumes/s (TITAN Xp, sliding 256-frame gate, 512 frames/s)"}
 
 

@@ -221,6 +221,17 @@ SSOCT_API ssoct_status ssoct_set_pupil(ssoct_plan plan, const double* coeffs, in
 SSOCT_API ssoct_status ssoct_sharpness(ssoct_plan plan, const uint16_t* frames_dev, float* vol_dev,
                                        double* out_host, void* stream);
 
+/* Sliding gates for display: the same gate update as ssoct_reconstruct_sliding
+ * (new frames through Eq. 5 + Eq. 6 only), then only the three cuts of its
+ * |V|^2 instead of the volume: xy[wy][wx] at depth bin z0 as one bin of Eq. 7
+ * per pixel, xz[nlambda][wx] at row y0 and yz[nlambda][wy] at column x0 (window
+ * coordinates) from Eq. 7 on the tiles that hold them.  Any output may be NULL.
+ * The cuts equal ssoct_get_cuts of the sliding volume (xz, yz bit for bit; xy
+ * to FP32 rounding).  EINVAL if a position lies outside the volume; otherwise as
+ * ssoct_reconstruct_sliding. */
+SSOCT_API ssoct_status ssoct_sliding_cuts(ssoct_plan plan, int x0, int y0, int z0, float* xy_dev, float* xz_dev,
+                                          float* yz_dev, void* stream);
+
 /* The three orthogonal cuts of a volume written by a reconstruct call with this
  * plan (text after Eq. 7; Fig. 5): xy[wy][wx] = P(x, y, z0), xz[nlambda][wx] =
  * P(x, y0, z), yz[nlambda][wy] = P(x0, y, z), coordinates in window pixels and

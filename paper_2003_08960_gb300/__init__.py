@@ -121,6 +121,11 @@ def ssoct_sharpness(plan, frames_ptr: int, vol_ptr: int, stream: int):
     return st, out
 
 
+def ssoct_sliding_cuts(plan, x0: int, y0: int, z0: int, xy_ptr: int, xz_ptr: int, yz_ptr: int, stream: int) -> int:
+    return _abi.lib().ssoct_sliding_cuts(plan, x0, y0, z0, C.c_void_p(xy_ptr or None), C.c_void_p(xz_ptr or None),
+                                         C.c_void_p(yz_ptr or None), C.c_void_p(stream))
+
+
 def ssoct_inject_stall(plan, skip: int, wait_limit_ns: int) -> int:
     """Test hook: make the next reconstructs skip `skip` work items so that
     dependent items time out after wait_limit_ns (see include/ssoct.h)."""
@@ -254,6 +259,17 @@ class Plan:
         _check(ssoct_reconstruct_sliding(self._h, vol.data_ptr(), cplx.data_ptr() if cplx is not None else 0,
                                          _stream_ptr(stream)), self._h, "reconstruct_sliding")
         return (vol, cplx) if complex_out else vol
+
+    def sliding_cuts(self, x0: int, y0: int, z0: int, stream=None):
+        """The three cuts of the sliding gate (see ssoct_sliding_cuts)."""
+        torch = _torch()
+        nl, wy, wx = self.volume_shape()
+        xy = torch.empty((wy, wx), dtype=torch.float32, device=self.device)
+        xz = torch.empty((nl, wx), dtype=torch.float32, device=self.device)
+        yz = torch.empty((nl, wy), dtype=torch.float32, device=self.device)
+        _check(ssoct_sliding_cuts(self._h, x0, y0, z0, xy.data_ptr(), xz.data_ptr(), yz.data_ptr(),
+                                  _stream_ptr(stream)), self._h, "sliding_cuts")
+        return xy, xz, yz
 
     def cuts(self, vol, x0: int, y0: int, z0: int, stream=None):
         torch = _torch()

@@ -74,6 +74,8 @@ SIGNATURES = {
     "ssoct_get_cuts": (C.c_int, [ssoct_plan, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ssoct_sync": (C.c_int, [ssoct_plan, C.c_void_p]),
+    "ssoct_sliding_cuts": (C.c_int, [ssoct_plan, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "ssoct_set_pupil": (C.c_int, [ssoct_plan, C.POINTER(C.c_double), C.c_int, C.c_double]),
     "ssoct_sharpness": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "ssoct_inject_stall": (C.c_int, [ssoct_plan, C.c_uint, C.c_ulonglong]),

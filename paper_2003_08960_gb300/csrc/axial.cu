@@ -120,6 +120,105 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(co
   });
 }
 
+struct GateCutsParams {
+  const float2* inter;   // [wy][ntx][nl][32]
+  const float2* wq;      // [nl] exp(-2 pi i k / nl)
+  const float2* twl;     // [N2l][N1l], sign - (the axial kernel's table)
+  float* xy;             // [wy][wx] or NULL
+  float* xz;             // [nl][wx] or NULL
+  float* yz;             // [nl][wy] or NULL
+  int nl, wx, wy, ntx, x0, y0, z0;
+  float power_scale;
+  int magnitude;
+};
+
+__device__ __forceinline__ float envelope(float2 v, float scale, int magnitude) {
+  const float pw = fmaf(v.x, v.x, v.y * v.y) * scale;
+  return magnitude ? sqrtf(pw) : pw;
+}
+
+// xy cut at depth bin z0 straight from the intermediate: at every window pixel
+// the single bin V_z0 = sum_t H_t exp(-2 pi i z0 t / N) of Eq. 7.
+__global__ void __launch_bounds__(256) gate_xy_kernel(const __grid_constant__ GateCutsParams c) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* w = reinterpret_cast<float2*>(smem);
+  for (int k = threadIdx.x; k < c.nl; k += blockDim.x) w[k] = ldg2(c.wq + k);
+  __syncthreads();
+  const size_t row = (size_t)c.ntx * kTile;
+  const size_t n = (size_t)c.wy * row;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int kyw = (int)(i / row), tile = (int)(i % row) / kTile, pix = (int)(i % kTile);
+    const int kxw = tile * kTile + pix;
+    const float2* h = c.inter + ((size_t)kyw * c.ntx + tile) * c.nl * kTile + pix;
+    float2 acc = make_float2(0.f, 0.f);
+    int k = 0;
+#pragma unroll 8
+    for (int t = 0; t < c.nl; ++t) {
+      const float2 v = __ldcs(h + (size_t)t * kTile);
+      const float2 e = w[k];
+      acc.x = fmaf(v.x, e.x, fmaf(-v.y, e.y, acc.x));
+      acc.y = fmaf(v.x, e.y, fmaf(v.y, e.x, acc.y));
+      k += c.z0;
+      if (k >= c.nl) k -= c.nl;
+    }
+    if (kxw < c.wx) c.xy[(size_t)kyw * c.wx + kxw] = envelope(acc, c.power_scale, c.magnitude);
+  }
+}
+
+// xz and yz cuts: the axial kernel's transform on the tiles of row y0 (blocks
+// 0 .. ntx-1) and on the tile holding column x0 of every row (the next wy
+// blocks), keeping only the cut's pixels.
+template <int NL>
+__global__ void __launch_bounds__(kTile * Split<NL>::N1) gate_lines_kernel(const __grid_constant__ GateCutsParams c) {
+  constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* ex = reinterpret_cast<float2*>(smem);
+  const bool xz_block = (int)blockIdx.x < c.ntx;
+  const int kyw = xz_block ? c.y0 : (int)blockIdx.x - c.ntx;
+  const int tile = xz_block ? (int)blockIdx.x : c.x0 / kTile;
+  const int pix = threadIdx.x % kTile, j1 = threadIdx.x / kTile;
+  const float2* src = c.inter + ((size_t)kyw * c.ntx + tile) * NL * kTile + pix;
+  float2 a[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) a[j2] = __ldcs(src + (j1 + N1 * j2) * kTile);
+  Dft<N2, -1>::template run<1, 0>(a);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(c.twl + k2 * N1 + j1));
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * kTile + pix] = a[k2];
+  __syncthreads();
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * kTile + pix];
+    Dft<N1, -1>::template run<1, i * N1>(a);
+  });
+  const int kxw = tile * kTile + pix;
+  if (kxw >= c.wx) return;
+  if (xz_block ? !c.xz : (!c.yz || kxw != c.x0)) return;
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const int q = k2 + N2 * k1;
+      const float pw = envelope(a[i * N1 + k1], c.power_scale, c.magnitude);
+      if (xz_block) c.xz[(size_t)q * c.wx + kxw] = pw;
+      else c.yz[(size_t)q * c.wy + kyw] = pw;
+    }
+  });
+}
+
+template <int NL>
+cudaError_t launch_lines(const GateCutsParams& c, cudaStream_t s) {
+  const size_t smem = (size_t)NL * kTile * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(gate_lines_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  gate_lines_kernel<NL><<<c.ntx + c.wy, kTile * Split<NL>::N1, smem, s>>>(c);
+  return cudaGetLastError();
+}
+
 template <int NL>
 cudaError_t launch_ra(const RescaleAxialParams& rp, cudaStream_t s) {
   const size_t smem = (size_t)NL * kTile * sizeof(float2);
@@ -142,6 +241,30 @@ cudaError_t launch(const AxialParams& ap, cudaStream_t s) {
 #define SSOCT_AXIAL_SIZES(X) X(16) X(32) X(64) X(96) X(128) X(160) X(200) X(256) X(512)
 
 }  // namespace
+
+cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, float* xz, float* yz, cudaStream_t s) {
+  GateCutsParams c;
+  c.inter = (const float2*)(p.ws + p.off_inter);
+  c.wq = (const float2*)(p.ws + p.off_wq);
+  c.twl = (const float2*)(p.ws + p.off_twl);
+  c.xy = xy;
+  c.xz = xz;
+  c.yz = yz;
+  c.nl = p.nl; c.wx = p.wx; c.wy = p.wy; c.ntx = p.ntx;
+  c.x0 = x0; c.y0 = y0; c.z0 = z0;
+  c.power_scale = (float)(p.alpha * p.alpha);
+  c.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  if (xy) {
+    gate_xy_kernel<<<4 * p.num_sms, 256, (size_t)p.nl * sizeof(float2), s>>>(c);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess || (!xz && !yz)) return e;
+#define X(a) if (p.nl == a) return launch_lines<a>(c, s);
+  SSOCT_AXIAL_SIZES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring_start, float2* planes,
                                  cudaStream_t s) {

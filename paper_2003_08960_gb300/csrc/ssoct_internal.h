@@ -158,6 +158,7 @@ struct Plan {
   // host tables
   std::vector<Tap> xtab, ytab;
   std::vector<float2> cx, cy, ox, oy, twx, twy, twl;
+  std::vector<float2> wq;   // [nl] exp(-2 pi i k / nl), for single-bin transforms
   std::vector<unsigned short> tcb;  // SSOCT_FLAG_TC_AXIAL: BF16 hi / lo 16-point DFT matrix (operand layout)
   // SSOCT_FLAG_PUPIL: input chirp x Zernike screen, its distance z and |K|, frames per Q chunk
   double sh_z = 0.0, sh_alpha = 0.0;
@@ -176,7 +177,7 @@ struct Plan {
   bool use_tc = false;       // axial pass on the tensor cores (flag, or the autotuner's choice)
   // workspace layout (byte offsets)
   size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_ox, off_oy, off_twx, off_twy, off_twl;
-  size_t off_tcb, off_ring, off_scratch, off_inter, ws_bytes;
+  size_t off_tcb, off_wq, off_ring, off_scratch, off_inter, ws_bytes;
   size_t off_cp = 0, off_F = 0, off_Q = 0, off_red = 0;  // SSOCT_FLAG_PUPIL regions
   // Frame sizes the persistent lateral kernel does not compile (384, 640, 768)
   // take the two-pass lateral path of sharpness.cu: chirp table and frame buffer.
@@ -211,6 +212,9 @@ struct Plan {
 cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s);
 cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s);
 cudaError_t launch_cuts(const CutsParams& cp, cudaStream_t s);
+// The three cuts of the current gate straight from the sweep-axis intermediate
+// (xy: one bin per pixel; xz, yz: the axial transform of the cut's tiles).
+cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, float* xz, float* yz, cudaStream_t s);
 // Axial-first order, first pass: Eq. 5 resample of every frame and Eq. 7 over
 // the sweep at every pixel, bins 0..nl/2 written as planes [nl/2 + 1][ny][nx].
 cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring_start, float2* planes,

@@ -265,6 +265,8 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.twx = twiddles(nx, p.n1x, p.n2x, +1);
   p.twy = twiddles(ny, p.n1y, p.n2y, +1);
   p.twl = twiddles(nlambda, p.n1l, p.n2l, -1);
+  p.wq.resize(nlambda);
+  for (int k = 0; k < nlambda; ++k) p.wq[k] = cis_pi(-2.0 * (double)k / nlambda);  // exp(-2 pi i k / nlambda)
   if (axial_tc_supported(nlambda)) axial_tc_table(p.tcb);  // kept for every such plan: the autotuner may switch forms
   p.use_tc = (flags & SSOCT_FLAG_TC_AXIAL) != 0;
 
@@ -311,6 +313,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_twy = take(sizeof(float2) * p.twy.size());
   p.off_twl = take(sizeof(float2) * p.twl.size());
   p.off_tcb = take(sizeof(unsigned short) * p.tcb.size());
+  p.off_wq = take(sizeof(float2) * p.wq.size());
   p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
   p.off_scratch = take(generic ? 0 : sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
   p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
@@ -373,6 +376,7 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
       {p.off_twy, p.twy.data(), sizeof(float2) * p.twy.size()},
       {p.off_twl, p.twl.data(), sizeof(float2) * p.twl.size()},
       {p.off_tcb, p.tcb.data(), sizeof(unsigned short) * p.tcb.size()},
+      {p.off_wq, p.wq.data(), sizeof(float2) * p.wq.size()},
   };
   for (const Up& u : ups) {
     if (!u.n) continue;
@@ -580,16 +584,13 @@ ssoct_status ssoct_reconstruct_frames(ssoct_plan h, const uint16_t* frames_dev, 
   return run_volume(p, frames_dev, 0, vol_dev, complex_dev, (cudaStream_t)stream);
 }
 
-ssoct_status ssoct_reconstruct_sliding(ssoct_plan h, float* vol_dev, void* complex_dev, void* stream) {
-  if (!h) return SSOCT_EINVAL;
-  Plan& p = h->p;
+// Lateral pass of the sliding gate: frames pushed since the last sliding call
+// (at most nl) into their slots of the intermediate; *ev gets the call's events.
+static ssoct_status sliding_update(Plan& p, cudaStream_t s, cudaEvent_t** ev_out) {
   if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
   if (p.generic) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need a frame size of the persistent lateral kernel");
   if (p.axial_first) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need the paper's order (no SSOCT_FLAG_AXIAL_FIRST)");
   if (p.stream_count < p.nl) return fail(&p, SSOCT_ENOTREADY, "fewer than nlambda frames pushed");
-  if (!vol_dev || ((uintptr_t)vol_dev % 16) || ((uintptr_t)complex_dev % 16))
-    return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
-  cudaStream_t s = (cudaStream_t)stream;
   // holograms still missing for the gate of the last nl frames: stream frames
   // [first, stream_count), in ring slots first % nl onwards
   const long long first = std::max(p.lat_upto, p.stream_count - p.nl);
@@ -620,7 +621,35 @@ ssoct_status ssoct_reconstruct_sliding(ssoct_plan h, float* vol_dev, void* compl
     cudaEventRecord(e0[1], s);
     ev = e0;
   }
+  *ev_out = ev;
+  return SSOCT_OK;
+}
+
+ssoct_status ssoct_reconstruct_sliding(ssoct_plan h, float* vol_dev, void* complex_dev, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (!vol_dev || ((uintptr_t)vol_dev % 16) || ((uintptr_t)complex_dev % 16))
+    return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t* ev = nullptr;
+  ssoct_status st = sliding_update(p, s, &ev);
+  if (st != SSOCT_OK) return st;
   return launch_axial_pass(p, vol_dev, complex_dev, s, ev);
+}
+
+ssoct_status ssoct_sliding_cuts(ssoct_plan h, int x0, int y0, int z0, float* xy, float* xz, float* yz, void* stream) {
+  if (!h) return SSOCT_EINVAL;
+  Plan& p = h->p;
+  if (x0 < 0 || x0 >= p.wx || y0 < 0 || y0 >= p.wy || z0 < 0 || z0 >= p.nl)
+    return fail(&p, SSOCT_EINVAL, "cut position outside the volume");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t* ev = nullptr;
+  ssoct_status st = sliding_update(p, s, &ev);
+  if (st != SSOCT_OK) return st;
+  const cudaError_t e = launch_gate_cuts(p, x0, y0, z0, xy, xz, yz, s);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "gate cuts kernels");
+  if (ev) cudaEventRecord(ev[2], s);
+  return SSOCT_OK;
 }
 
 ssoct_status ssoct_get_cuts(ssoct_plan h, const float* vol_dev, int x0, int y0, int z0, float* xy,

@@ -362,3 +362,29 @@ def test_axial_first_paper_size_1024x1024x256(ss):
     plan, vol, cplx, ref = _run(ss, w, method="fft", flags=ss.SSOCT_FLAG_AXIAL_FIRST)
     err = _check(vol, cplx, ref)
     print(f"axial-first 1024x1024x256 complex rel L2 = {err:.3e}")
+
+
+def test_sliding_cuts_only(ss):
+    """Cuts-only sliding gates give the cuts of the sliding volume: xz and yz bit
+    for bit (same transform), xy to FP32 rounding (one-bin sum instead of the
+    FFT); a window and a ragged tile are included."""
+    a = synth.workload("tiny_64x64x32", seed=1)
+    b = synth.workload("tiny_64x64x32", seed=7)
+    stream = np.concatenate([a.frames, b.frames])
+    win = (6, 10, 50, 37)
+    full = ss.Plan(a.nx, a.ny, a.nlambda, a.pitch, a.z, a.lambdas, window=win)
+    cuts = ss.Plan(a.nx, a.ny, a.nlambda, a.pitch, a.z, a.lambdas, window=win)
+    pushed = 0
+    for step, (x0, y0, z0) in zip((32, 13, 5, 0, 14), [(3, 4, 5), (49, 36, 31), (0, 0, 0), (33, 17, 12), (20, 30, 7)]):
+        if step:
+            f = _dev(stream[pushed:pushed + step])
+            assert full.push(f) == ss.SSOCT_OK and cuts.push(f) == ss.SSOCT_OK
+            pushed += step
+        vol = full.reconstruct_sliding()
+        xy_ref, xz_ref, yz_ref = full.cuts(vol, x0, y0, z0)
+        xy, xz, yz = cuts.sliding_cuts(x0, y0, z0)
+        torch.cuda.synchronize()
+        assert torch.equal(xz, xz_ref) and torch.equal(yz, yz_ref)
+        assert torch.allclose(xy, xy_ref, rtol=1e-4, atol=1e-6 * float(xy_ref.max()))
+    with pytest.raises(ss.SsoctError):
+        cuts.sliding_cuts(50, 0, 0)
