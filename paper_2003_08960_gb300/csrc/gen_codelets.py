@@ -12,8 +12,9 @@ which replaces x[OFF + k*ST], k = 0..R-1, by sum_j x[OFF + j*ST] exp(SIGN 2 pi i
 (unnormalised, natural order in and out).  Indices are compile-time constants, so
 a register array passed in stays in registers.
 
-Power-of-two sizes use radix-2 decimation in time with the trivial twiddles
-(1, +-i, (+-1 +- i)/sqrt 2) expanded into additions; sizes 3 and 5 use the
+Power-of-two sizes use split-radix decimation in time (Duhamel and Hollmann,
+1984) with the trivial twiddles (1, +-i, (+-1 +- i)/sqrt 2) expanded into
+additions; sizes 3 and 5 use the
 direct real/imaginary symmetric form; composite sizes with a factor 3 or 5 use
 one mixed-radix (Cooley-Tukey) split.  Twiddle constants are computed here in
 float64 and rounded once to float32.
@@ -109,15 +110,8 @@ class Gen:
             return self.dft3(xs, sign)
         if n == 5:
             return self.dft5(xs, sign)
-        if n % 2 == 0 and (n & (n - 1)) == 0:
-            ev = self.dft(xs[0::2], sign)
-            od = self.dft(xs[1::2], sign)
-            out = [None] * n
-            for k in range(n // 2):
-                t = self.twiddle(od[k], k, n, sign)
-                out[k] = self.add(ev[k], t)
-                out[k + n // 2] = self.sub(ev[k], t)
-            return out
+        if n % 4 == 0 and (n & (n - 1)) == 0:
+            return self.split_radix(xs, sign)
         # mixed radix: n = p * m with p the smallest prime factor in {2,3,5}
         for p in (2, 3, 5):
             if n % p == 0:
@@ -133,6 +127,40 @@ class Gen:
             res = self.dft(col, sign)                               # length p, index k1
             for k1 in range(p):
                 out[k2 + m * k1] = res[k1]
+        return out
+
+    def mul_i(self, a, s):
+        """a * (s i), s = +-1: a swap and a negation, no arithmetic."""
+        v = self.var()
+        if s > 0:
+            self.emit(f"const float2 {v} = make_float2(-{a}.y, {a}.x);")
+        else:
+            self.emit(f"const float2 {v} = make_float2({a}.y, -{a}.x);")
+        return v
+
+    def split_radix(self, xs, sign):
+        """Split-radix decimation in time (Duhamel and Hollmann, 1984), n a power
+        of two >= 4: U = DFT_{n/2} of the even samples, Z and Z' = DFT_{n/4} of
+        the samples 4m+1 and 4m+3.  With W = exp(sign 2 pi i / n),
+        t1 = W^k Z[k], t2 = W^{3k} Z'[k], s = t1 + t2, d = t1 - t2:
+            X[k]        = U[k] + s          X[k + n/2]  = U[k] - s
+            X[k + n/4]  = U[k + n/4] + sign i d
+            X[k + 3n/4] = U[k + n/4] - sign i d        (k = 0 .. n/4 - 1)."""
+        n = len(xs)
+        u = self.dft(xs[0::2], sign)
+        z1 = self.dft(xs[1::4], sign)
+        z3 = self.dft(xs[3::4], sign)
+        out = [None] * n
+        q = n // 4
+        for k in range(q):
+            t1 = self.twiddle(z1[k], k, n, sign)
+            t2 = self.twiddle(z3[k], 3 * k, n, sign)
+            sm = self.add(t1, t2)
+            df = self.mul_i(self.sub(t1, t2), sign)
+            out[k] = self.add(u[k], sm)
+            out[k + 2 * q] = self.sub(u[k], sm)
+            out[k + q] = self.add(u[k + q], df)
+            out[k + 3 * q] = self.sub(u[k + q], df)
         return out
 
     def dft3(self, xs, sign):

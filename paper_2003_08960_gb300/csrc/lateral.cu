@@ -1,15 +1,17 @@
 // Lateral stage: chromatic rescale (Eq. 5) + Fresnel transform (Eq. 6) of every
 // frame of a sweep, as one persistent, warp-specialised kernel.
 //
-// Each CTA has one producer warp and eight consumer warps.  The producer takes
-// work items from a device ticket counter (in the order LateralSchedule
-// defines), waits until an item's inputs are ready, and copies them into one of
-// three shared-memory stage buffers with the Tensor Memory Accelerator (1D bulk
-// copies of the uint16 input rows and tap tables, or 2D tensor copies of an L2
-// scratch column band), handing the item over through an mbarrier.  Consumers
-// only compute, in place in the stage buffer; when they are done they arrive on
-// a second mbarrier, and the producer writes the item's outputs with TMA stores
-// (whole-frame plans) and publishes the item's completion to the other CTAs.
+// Each CTA has a producer warp, two consumer groups of eight warps and a
+// publisher warp.  The producer takes work items from a device ticket counter
+// (in the order LateralSchedule defines), waits until an item's inputs are
+// ready, and copies them into one of three shared-memory stage buffers with the
+// Tensor Memory Accelerator (1D bulk copies of the uint16 input rows and tap
+// tables, or 2D tensor copies of an L2 scratch column band), handing the item
+// over through an mbarrier; hand-overs alternate between the two consumer
+// groups, so two items are computed at once.  Consumers compute in place in the
+// stage buffer, store the item's outputs themselves and arrive on a second
+// mbarrier; the publisher then makes the outputs visible to the other CTAs
+// (release increment of the frame's counter), off the producer's path.
 // Items:
 //  * row item (frame f, band of rows): stage the input rows the band needs in
 //    shared memory as float, resample them with the frame's separable linear-
@@ -31,7 +33,8 @@
 namespace ssoct {
 namespace {
 
-constexpr int kCtaThreads = kThreads + 32;            // 8 consumer warps + 1 producer warp
+constexpr int kGroups = 2;                            // consumer groups, each works on its own item
+constexpr int kCtaThreads = kGroups * kThreads + 64;  // 2 x 8 consumer warps, a producer and a publisher warp
 constexpr unsigned long long kProducerWaitNs = 2000000000ull;   // 2 s
 constexpr unsigned long long kConsumerWaitNs = 4000000000ull;   // longer: the producer gives up first
 enum : int { kRowItem = 0, kColItem = 1, kEndItem = 2 };
@@ -110,60 +113,37 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// 1D bulk copy shared -> global with an L2 policy (bulk async-group of the
-// issuing thread).
-__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, unsigned bytes, unsigned long long pol) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
-               "r"(smem_u32(src)), "r"(bytes), "l"(pol)
-               : "memory");
-}
-// 2D tiled tensor copy shared -> global (box as set in the tensor map), L2 policy.
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src,
-                                             unsigned long long pol) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
-                   map),
-               "r"(x), "r"(y), "r"(smem_u32(src)), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// every committed group of this thread has finished reading shared memory
-__device__ __forceinline__ void bulk_wait_reads() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// every committed group of this thread has finished writing global memory
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// every committed group but the most recent one has finished writing
-__device__ __forceinline__ void bulk_wait_all_but_last() {
-  asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
-}
-// Order this thread's generic-proxy shared-memory writes before later async-proxy
-// (TMA) reads of them, and generic / async global accesses against each other.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
+// Order generic and async-proxy (TMA) global accesses against each other.
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Barrier of the consumer warps only (named barrier 1); returns the OR of `v`.
-__device__ __forceinline__ bool consumers_sync_or(bool v) {
+// Barrier of consumer group g only (named barrier 1 + g); returns the OR of `v`.
+__device__ __forceinline__ bool consumers_sync_or(int g, bool v) {
   unsigned r;
-  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
-               : "=r"(r)
-               : "r"((unsigned)v), "n"(kThreads)
-               : "memory");
+  if (g == 0)
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((unsigned)v), "n"(kThreads)
+                 : "memory");
+  else
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 2, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((unsigned)v), "n"(kThreads)
+                 : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+__device__ __forceinline__ void consumers_sync(int g) {
+  if (g == 0) asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+  else asm volatile("bar.sync 2, %0;" ::"n"(kThreads) : "memory");
+}
 
 // ---------------------------------------------------------------- consumer work
 
 constexpr int kStages = 3;  // stage buffers: one computed, one or two loaded ahead
-// Whole-frame outputs leave through producer-issued TMA stores (true) or direct
-// consumer stores (false).  Measured on GB300 at 1024 x 1024 x 256: TMA stores
-// free the consumers (row items 6.5 k instead of 8.2 k cycles, column items 3.9 k
-// instead of 6.2 k) but the single producer thread then serialises on writing
-// and waiting for 1024 64-byte column rows per band, and consumers idle; direct
-// stores are faster overall (1.72 ms vs 1.87 ms per volume).
-constexpr bool kTmaOut = false;
+// Items' outputs leave through the consumers' own stores.  (Producer-issued TMA
+// stores of them were measured slower on GB300: the single producer thread
+// serialises on writing and waiting for 1024 64-byte column rows per band.)
 
 // A row item's stage buffer: nrows uint16 input rows, then (16-byte aligned) the
 // frame's NX x taps, the RPI y taps and the RPI y chirps of its rows.
@@ -194,10 +174,10 @@ __device__ __forceinline__ float u16_to_f(unsigned short u) {
 // transpose block and, for whole-frame plans, as the output [RPI][NX].
 template <int NX, int NY, bool FW, bool AF>
 __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, unsigned char* buf,
-                                         const float2* twx, const float2* cxs) {
+                                         const float2* twx, const float2* cxs, int g) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
   constexpr int RPI = kThreads / N1;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x % kThreads;
   const int r = tid / N1;
   const int j1 = tid % N1;
   const int f = d.f;
@@ -243,7 +223,7 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   Dft<N2, 1>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
-  consumers_sync();  // every input of the buffer has been read
+  consumers_sync(g);  // every input of the buffer has been read
   float2* ex = reinterpret_cast<float2*>(buf) + r * NX;  // this row's block (N2 x N1 = NX values)
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) ex[xswz<N1>(k2, j1)] = a[k2];
@@ -255,18 +235,7 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
     for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[xswz<N1>(k2, jj)];
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
-  if constexpr (FW && kTmaOut) {
-    // 3. the row in natural order over its own block; the producer writes the
-    //    RPI rows to the scratch slot with TMA
-    __syncwarp();
-    static_for<0, N2 / N1>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const int k2 = j1 + N1 * i;
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) ex[k2 + N2 * k1] = a[i * N1 + k1];
-    });
-    fence_proxy_async_smem();
-  } else {
+  {
     // 3. window columns straight into the scratch slot of frame f
     const unsigned long long pol_last = policy_evict_last();
     float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
@@ -292,10 +261,10 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
 // producer's tensor store.
 template <int NY, bool FW, bool AF>
 __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, unsigned char* buf,
-                                         const float2* twy) {
+                                         const float2* twy, int g) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x % kThreads;
   const int b = tid % BC;
   const int j1 = tid / BC;
   float2* tile = reinterpret_cast<float2*>(buf);
@@ -307,7 +276,7 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], twy[k2 * N1 + j1]);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) tile[(j1 + N1 * k2) * BC + b] = a[k2];  // the rows this thread read
-  consumers_sync();
+  consumers_sync(g);
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
@@ -341,15 +310,6 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
         }
       });
     }
-  } else if constexpr (FW && kTmaOut) {
-    consumers_sync();  // every transposed read is done
-    static_for<0, N2 / N1>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const int k2 = j1 + N1 * i;
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) tile[(k2 + N2 * k1) * BC + b] = a[i * N1 + k1];
-    });
-    fence_proxy_async_smem();
   } else {
     const int kxw = d.item * BC + b;
     if (kxw < p.wx) {
@@ -375,127 +335,50 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
 
 // ---------------------------------------------------------------- producer
 
-// Producer warp, one thread.  Stage buffer b holds at most one item from its
-// hand-over until (a) the consumers arrive on done[b] and, for whole-frame plans,
-// (b) the TMA stores of the item's outputs have read the buffer.  An item is
-// published to other CTAs (red.release on its frame's counter) once its outputs
-// are in global memory: right after done[b] when the consumers stored them,
-// after the TMA writes complete otherwise.  Every wait keeps servicing finished
-// items, so a CTA never holds back a completion another CTA is waiting for.
+// Hand-over bookkeeping in shared memory between the producer and the
+// publisher.  The producer runs at most kStages hand-overs ahead of the
+// publisher, so kPubQ > kStages slots of item info suffice.
+constexpr int kPubQ = 4;
+struct Handover {
+  int kind[kPubQ];
+  int f[kPubQ];
+  unsigned handed;     // items handed over so far (producer)
+  unsigned finished;   // 1: the producer hands over no more items
+  unsigned published;  // items published so far (publisher)
+};
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* a) { return *(const volatile unsigned*)a; }
+__device__ __forceinline__ void st_volatile_u32(unsigned* a, unsigned v) { *(volatile unsigned*)a = v; }
+
+// Producer warp, one thread.  For hand-over s (item or end mark) it takes a
+// ticket, waits (bounded) for the item's dependency on other CTAs, waits until
+// hand-over s - kStages, the previous user of stage buffer s mod kStages, has
+// been published (so its consumers are done), copies the item's inputs into the
+// buffer with TMA and hands it over; hand-over s goes to consumer group
+// s mod kGroups, and each group gets one end mark.  It publishes nothing: the
+// publisher does, so the release of one item's outputs (a wait for its stores)
+// never delays preparing the next.  A CTA holds at most one unstarted ticket
+// and every dependency is on lower tickets, so the queue drains.
 template <int NX, int NY, bool FW, bool AF>
-__device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const CUtensorMap* tmap_inter,
-                         uint64_t* full_bar, uint64_t* done_bar, Desc* desc, unsigned char* stage0) {
+__device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64_t* full_bar, Desc* desc,
+                         unsigned char* stage0, Handover* ho) {
   constexpr int RPI = kThreads / Split<NX>::N1;
   constexpr int BC = kThreads / Split<NY>::N1;
   constexpr int BOX_ROWS = NY < 256 ? NY : 256;
   const long long total = p.sch.total();
-  int st_kind[kStages], st_f[kStages], st_item[kStages];
-  bool st_storing[kStages];
-  unsigned phase[kStages];
-#pragma unroll
-  for (int b = 0; b < kStages; ++b) {
-    st_kind[b] = -1;
-    st_f[b] = st_item[b] = 0;
-    st_storing[b] = false;
-    phase[b] = 0u;
-  }
-  int pend_n = 0, pend_kind[kStages], pend_f[kStages];
-  const unsigned long long pol_last = policy_evict_last();
-  const unsigned long long pol_first = policy_evict_first();
-  auto publish = [&](int kind, int f) { red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u); };
-  // publish items whose TMA writes are complete (pend_* in commit order, one
-  // bulk group per item)
-  auto flush = [&]() {
-    if (pend_n) {
-      bulk_wait_all();
-      fence_proxy_async_global();
-      for (int i = 0; i < pend_n; ++i) publish(pend_kind[i], pend_f[i]);
-      pend_n = 0;
-    }
-  };
-  // publish all but the newest: the older groups were issued at least one item
-  // ago, so this rarely waits
-  auto flush_older = [&]() {
-    if (pend_n >= 2) {
-      bulk_wait_all_but_last();
-      fence_proxy_async_global();
-      for (int i = 0; i + 1 < pend_n; ++i) publish(pend_kind[i], pend_f[i]);
-      pend_kind[0] = pend_kind[pend_n - 1];
-      pend_f[0] = pend_f[pend_n - 1];
-      pend_n = 1;
-    }
-  };
-  // free the buffers whose TMA stores have read them
-  auto release_reads = [&]() {
-    bool any = false;
-#pragma unroll
-    for (int b = 0; b < kStages; ++b) any |= st_storing[b];
-    if (!any) return;
-    bulk_wait_reads();
-#pragma unroll
-    for (int b = 0; b < kStages; ++b)
-      if (st_storing[b]) {
-        st_storing[b] = false;
-        st_kind[b] = -1;
-      }
-  };
-  auto finish = [&](int b) {
-    phase[b] ^= 1u;
-    if constexpr (FW && kTmaOut) {
-      const unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
-      if (st_kind[b] == kRowItem) {
-        // eight contiguous rows: quick to write, and column items of this frame
-        // are waiting for them, so publish as soon as they are written
-        float2* dst = p.scratch + ((size_t)(st_f[b] % p.sch.slots) * NY + st_item[b] * RPI) * p.wxp;
-#pragma unroll 1
-        for (int r = 0; r < RPI; ++r)
-          tma_store_1d(dst + (size_t)r * p.wxp, buf + (size_t)r * NX * sizeof(float2), (unsigned)(NX * sizeof(float2)),
-                       pol_last);
-        bulk_commit();
-        flush();  // every group, this one included
-        publish(kRowItem, st_f[b]);
-        st_kind[b] = -1;
-      } else {
-        // a column band: many short rows, slower to write; only the reuse of its
-        // scratch slot (several frames later) waits for it, so publish lazily
-        const int b0 = st_item[b] * BC;
-        const int x = 2 * (((b0 / kTile) * p.nl + (p.tab0 + st_f[b]) % p.nl) * kTile + (b0 % kTile));
-#pragma unroll
-        for (int i = 0; i < NY / BOX_ROWS; ++i)
-          tma_store_2d(tmap_inter, x, i * BOX_ROWS, buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), pol_first);
-        bulk_commit();
-        if (pend_n == kStages) flush();
-        pend_kind[pend_n] = st_kind[b];
-        pend_f[pend_n] = st_f[b];
-        ++pend_n;
-        st_storing[b] = true;
-      }
-    } else {
-      publish(st_kind[b], st_f[b]);
-      st_kind[b] = -1;
-    }
-  };
-  auto service = [&]() {
-#pragma unroll
-    for (int b = 0; b < kStages; ++b)
-      if (st_kind[b] >= 0 && !st_storing[b] && mbar_test(&done_bar[b], phase[b])) finish(b);
-  };
   auto give_up = [&]() {
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
     atomicExch(&p.ctr->abort, 1u);
   };
   const unsigned long long wait_limit = p.wait_ns ? p.wait_ns : kProducerWaitNs;
-  // The producer prepares item s (ticket, dependency, descriptor) before its
-  // buffer is free, and only the copy issue waits for the buffer.  A CTA holds
-  // at most one unstarted, unpublished ticket; the lowest unfinished ticket is
-  // always one its CTA is working on or has handed over, so the queue drains.
   unsigned t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-  int b = 0;
-  for (;; b = (b + 1 == kStages) ? 0 : b + 1) {
+  int ends = 0;
+  for (unsigned s = 0;; ++s) {
+    const int b = (int)(s % kStages);
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     const unsigned t = t_next;
     int kind = kEndItem, f = 0, item = 0;
-    if (t < total) p.sch.decode(t, kind, f, item);
+    if (t < total && ends == 0) p.sch.decode(t, kind, f, item);
     // 1. its dependency: a column item needs every row item of its frame; a row
     //    item needs the columns of the frame whose scratch slot it reuses
     if (kind != kEndItem) {
@@ -511,9 +394,6 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       if (dep && ld_acquire_gpu(dep) < target) {
         const unsigned long long t0 = global_timer_ns();
         while (ld_acquire_gpu(dep) < target) {
-          service();
-          release_reads();
-          flush();
           if (*(volatile unsigned*)&p.ctr->abort || global_timer_ns() - t0 > wait_limit) {
             give_up();
             kind = kEndItem;
@@ -531,17 +411,13 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       d.jlo = yt[item * RPI].base;
       d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
     }
-    // 2. the buffer's previous item must be finished (and its stores must have
-    //    read it)
-    if (st_kind[b] >= 0) {
+    // 2. the buffer's previous hand-over must be published (its consumers done)
+    if (s >= (unsigned)kStages && ld_volatile_u32(&ho->published) + kStages <= s) {
       const unsigned long long t0 = global_timer_ns();
-      while (st_kind[b] >= 0) {
-        service();
-        if (st_kind[b] >= 0 && st_storing[b]) release_reads();
-        if (st_kind[b] >= 0) flush();
-        if (st_kind[b] >= 0 && global_timer_ns() - t0 > wait_limit) {
+      while (ld_volatile_u32(&ho->published) + kStages <= s) {
+        if (global_timer_ns() - t0 > wait_limit) {
           give_up();
-          kind = kEndItem;  // the buffer's old item is lost; consumers still get an end mark
+          kind = kEndItem;  // the buffer's old item is lost; the consumers still get end marks
           break;
         }
       }
@@ -550,8 +426,11 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
     if (kind == kEndItem) {
       desc[b] = Desc{kEndItem, 0, 0, 0, 0, 0};
       mbar_arrive(&full_bar[b]);
-      break;
+      if (++ends == kGroups) break;
+      continue;
     }
+    ho->kind[s % kPubQ] = kind;
+    ho->f[s % kPubQ] = f;
     desc[b] = d;
     if (AF && kind == kRowItem) {
       // RPI contiguous rows of the half-spectrum plane of bin af_bin(f)
@@ -580,30 +459,59 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, const 
       for (int i = 0; i < NY / BOX_ROWS; ++i)
         tma_load_2d(buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), tmap, x, y0 + i * BOX_ROWS, &full_bar[b]);
     }
-    st_kind[b] = kind;
-    st_f[b] = f;
-    st_item[b] = item;
-    // the next ticket, requested once this one is handed over (its round trip
-    // overlaps the wait for the next free buffer)
+    __threadfence_block();
+    st_volatile_u32(&ho->handed, s + 1);
+    // the next ticket, requested once this one is handed over
     t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-    service();
-    flush_older();
   }
-  // drain: publish what is still in flight
-  const unsigned long long t0 = global_timer_ns();
-  for (;;) {
-    service();
-    release_reads();
-    bool busy = false;
-#pragma unroll
-    for (int i = 0; i < kStages; ++i) busy |= st_kind[i] >= 0;
-    if (!busy) break;
-    if (global_timer_ns() - t0 > wait_limit) {
-      give_up();
-      break;
+  __threadfence_block();
+  st_volatile_u32(&ho->finished, 1u);
+}
+
+// Publisher warp, one thread: in hand-over order, waits (bounded) until the
+// item's consumers arrive on its buffer's done barrier, then publishes it to
+// other CTAs with a release increment of its frame's counter, which orders the
+// item's outputs (the consumers' stores) before it at GPU scope.
+__device__ void publisher(const LateralParams& p, uint64_t* done_bar, Handover* ho) {
+  auto give_up = [&]() {
+    atomicCAS(&p.ctr->err, 0u, kErrTimeout);
+    atomicExch(&p.ctr->abort, 1u);
+  };
+  const unsigned long long wait_limit = p.wait_ns ? p.wait_ns : kProducerWaitNs;
+  for (unsigned s = 0;; ++s) {
+    if (ld_volatile_u32(&ho->handed) <= s) {
+      const unsigned long long t0 = global_timer_ns();
+      for (;;) {
+        if (ld_volatile_u32(&ho->handed) > s) break;
+        if (ld_volatile_u32(&ho->finished)) {
+          __threadfence_block();
+          if (ld_volatile_u32(&ho->handed) <= s) return;  // everything handed over is published
+          break;
+        }
+        if (global_timer_ns() - t0 > 2 * wait_limit) {
+          give_up();
+          return;
+        }
+        __nanosleep(32);
+      }
     }
+    __threadfence_block();
+    const int kind = ho->kind[s % kPubQ];
+    const int f = ho->f[s % kPubQ];
+    const int b = (int)(s % kStages);
+    const unsigned parity = (s / kStages) & 1u;
+    if (!mbar_test(&done_bar[b], parity)) {
+      const unsigned long long t0 = global_timer_ns();
+      while (!mbar_test(&done_bar[b], parity)) {
+        if (global_timer_ns() - t0 > 2 * wait_limit) {
+          give_up();
+          return;
+        }
+      }
+    }
+    red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u);
+    st_volatile_u32(&ho->published, s + 1);
   }
-  flush();
 }
 
 template <int NX, int NY, bool FW, bool AF>
@@ -617,8 +525,12 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t done_bar[kStages];
   __shared__ Desc desc[kStages];
+  __shared__ Handover ho;
   const int tid = threadIdx.x;
   if (tid == 0) {
+    ho.handed = 0u;
+    ho.finished = 0u;
+    ho.published = 0u;
 #pragma unroll
     for (int b = 0; b < kStages; ++b) {
       mbar_init(&full_bar[b], 1);
@@ -631,36 +543,37 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   float2* twx = reinterpret_cast<float2*>(smem + kStages * (size_t)p.stage_bytes);
   float2* twy = twx + NX;
   float2* cxs = twy + NY;
-  if (tid >= kThreads) {
-    if (tid == kThreads) producer<NX, NY, FW, AF>(p, &tmap, &tmap_inter, full_bar, done_bar, desc, stage0);
+  if (tid >= kGroups * kThreads) {
+    if (tid == kGroups * kThreads) producer<NX, NY, FW, AF>(p, &tmap, full_bar, desc, stage0, &ho);
+    if (tid == kGroups * kThreads + 32) publisher(p, done_bar, &ho);
     return;
   }
-  for (int i = tid; i < NX; i += kThreads) {
+  for (int i = tid; i < NX; i += kGroups * kThreads) {
     twx[i] = ldg2(p.twx + i);
     cxs[i] = ldg2(p.cx + i);
   }
-  for (int i = tid; i < NY; i += kThreads) twy[i] = ldg2(p.twy + i);
-  // (visible to all consumers after the first consumers_sync_or below)
-  int b = 0;
-  unsigned use = 0;  // completions of full[b] seen so far, per pass over the buffers
-  for (;;) {
+  for (int i = tid; i < NY; i += kGroups * kThreads) twy[i] = ldg2(p.twy + i);
+  asm volatile("bar.sync 3, %0;" ::"n"(kGroups * kThreads) : "memory");  // tables seen by both groups
+  // Group g takes hand-overs s = g, g + kGroups, ...: buffer s mod kStages, the
+  // (s / kStages)-th fill of that buffer.  The buffer's previous fill (s -
+  // kStages) went to the other group and preceded this group's previous one, so
+  // the parity wait cannot pass early.
+  const int g = tid / kThreads;
+  for (unsigned s = g;; s += kGroups) {
+    const int b = (int)(s % kStages);
     // consumers wait longer than the producer, which gives up first and hands
-    // them an end mark
-    const bool ok = mbar_wait(&full_bar[b], use & 1u, p.ctr, p.wait_ns ? 2 * p.wait_ns : kConsumerWaitNs);
-    // all consumers agree, and the previous item is finished everywhere
-    if (consumers_sync_or(!ok)) break;
+    // each group an end mark
+    const bool ok = mbar_wait(&full_bar[b], (s / kStages) & 1u, p.ctr, p.wait_ns ? 2 * p.wait_ns : kConsumerWaitNs);
+    // the group agrees, and its previous item is finished in all its threads
+    if (consumers_sync_or(g, !ok)) break;
     const Desc d = desc[b];
     if (d.kind == kEndItem) break;
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
     if (d.kind == kRowItem)
-      row_item<NX, NY, FW, AF>(p, d, buf, twx, cxs);
+      row_item<NX, NY, FW, AF>(p, d, buf, twx, cxs, g);
     else
-      col_item<NY, FW, AF>(p, d, buf, twy);
+      col_item<NY, FW, AF>(p, d, buf, twy, g);
     mbar_arrive(&done_bar[b]);
-    if (++b == kStages) {
-      b = 0;
-      ++use;
-    }
   }
 }
 
