@@ -1,14 +1,14 @@
 // Lateral stage: chromatic rescale (Eq. 5) + Fresnel transform (Eq. 6) of every
 // frame of a sweep, as one persistent, warp-specialised kernel.
 //
-// Each CTA has a producer warp, two consumer groups of eight warps and a
-// publisher warp.  The producer takes work items from a device ticket counter
-// (in the order LateralSchedule defines), waits until an item's inputs are
-// ready, and copies them into one of three shared-memory stage buffers with the
-// Tensor Memory Accelerator (1D bulk copies of the uint16 input rows and tap
-// tables, or 2D tensor copies of an L2 scratch column band), handing the item
-// over through an mbarrier; hand-overs alternate between the two consumer
-// groups, so two items are computed at once.  Consumers compute in place in the
+// Each CTA has two producer warps, two consumer groups of eight warps and a
+// publisher warp.  A producer takes work items from a device ticket counter (in
+// the order LateralSchedule defines), waits until an item's inputs are ready,
+// and copies them into one of three shared-memory stage buffers with the Tensor
+// Memory Accelerator (1D bulk copies of the uint16 input rows and tap tables,
+// or 2D tensor copies of an L2 scratch column band), handing the item over
+// through an mbarrier; producer g feeds consumer group g, hand-overs alternate
+// between them, and two items are computed at once.  Consumers compute in place in the
 // stage buffer, store the item's outputs themselves and arrive on a second
 // mbarrier; the publisher then makes the outputs visible to the other CTAs
 // (release increment of the frame's counter), off the producer's path.
@@ -34,7 +34,7 @@ namespace ssoct {
 namespace {
 
 constexpr int kGroups = 2;                            // consumer groups, each works on its own item
-constexpr int kCtaThreads = kGroups * kThreads + 64;  // 2 x 8 consumer warps, a producer and a publisher warp
+constexpr int kCtaThreads = kGroups * kThreads + 96;  // 2 x 8 consumer warps, 2 producer warps, a publisher warp
 constexpr unsigned long long kProducerWaitNs = 2000000000ull;   // 2 s
 constexpr unsigned long long kConsumerWaitNs = 4000000000ull;   // longer: the producer gives up first
 enum : int { kRowItem = 0, kColItem = 1, kEndItem = 2 };
@@ -335,50 +335,94 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
 
 // ---------------------------------------------------------------- producer
 
-// Hand-over bookkeeping in shared memory between the producer and the
-// publisher.  The producer runs at most kStages hand-overs ahead of the
-// publisher, so kPubQ > kStages slots of item info suffice.
+// Hand-over bookkeeping in shared memory between the producers and the
+// publisher.  Hand-over s is prepared by producer s mod kProducers and computed
+// by consumer group s mod kGroups (kProducers == kGroups: producer g feeds group
+// g).  Producer 0 claims tickets in pairs, so hand-over positions follow ticket
+// order.  Producers run at most kStages positions ahead of the publisher, so
+// kPubQ > kStages slots of item info suffice.
+constexpr int kProducers = kGroups;
 constexpr int kPubQ = 4;
+constexpr int kTicketQ = 4;
+// Full barriers: one per position mod lcm(kStages, kGroups), so that each is
+// filled by one producer in position order and waited on by one group, which
+// has consumed its previous fill: parity waits cannot pass early even though
+// the two producers' hand-overs may complete out of order.
+constexpr int kFullBars = kStages * kGroups;
+constexpr unsigned kEndStamp = 0x80000000u;
 struct Handover {
   int kind[kPubQ];
   int f[kPubQ];
-  unsigned handed;     // items handed over so far (producer)
-  unsigned finished;   // 1: the producer hands over no more items
-  unsigned published;  // items published so far (publisher)
+  unsigned stamp[kPubQ];     // s + 1 once hand-over s is in place (| kEndStamp for an end mark)
+  unsigned published;        // hand-overs published so far (publisher)
+  unsigned tk[kTicketQ];     // ticket of position 2k + 1, from producer 0 to producer 1
+  unsigned tk_stamp[kTicketQ];
 };
 
 __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* a) { return *(const volatile unsigned*)a; }
 __device__ __forceinline__ void st_volatile_u32(unsigned* a, unsigned v) { *(volatile unsigned*)a = v; }
 
-// Producer warp, one thread.  For hand-over s (item or end mark) it takes a
-// ticket, waits (bounded) for the item's dependency on other CTAs, waits until
-// hand-over s - kStages, the previous user of stage buffer s mod kStages, has
-// been published (so its consumers are done), copies the item's inputs into the
-// buffer with TMA and hands it over; hand-over s goes to consumer group
-// s mod kGroups, and each group gets one end mark.  It publishes nothing: the
-// publisher does, so the release of one item's outputs (a wait for its stores)
-// never delays preparing the next.  A CTA holds at most one unstarted ticket
+// Producer warp pi (one thread each), hand-over positions s = 2k + pi.  For
+// each it takes the position's ticket, waits (bounded) for the item's
+// dependency on other CTAs, waits until hand-over s - kStages, the previous user
+// of stage buffer s mod kStages, has been published (so its consumers are
+// done), copies the item's inputs into the buffer with TMA and hands it over to
+// consumer group pi; its last hand-over is that group's end mark.  It publishes
+// nothing: the publisher does, so the release of one item's outputs (a wait for
+// its stores) never delays preparing the next.  Positions follow ticket order
 // and every dependency is on lower tickets, so the queue drains.
 template <int NX, int NY, bool FW, bool AF>
 __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64_t* full_bar, Desc* desc,
-                         unsigned char* stage0, Handover* ho) {
+                         unsigned char* stage0, Handover* ho, int pi) {
   constexpr int RPI = kThreads / Split<NX>::N1;
   constexpr int BC = kThreads / Split<NY>::N1;
   constexpr int BOX_ROWS = NY < 256 ? NY : 256;
-  const long long total = p.sch.total();
+  const unsigned total = (unsigned)p.sch.total();
   auto give_up = [&]() {
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
     atomicExch(&p.ctr->abort, 1u);
   };
+  auto aborted = [&]() { return *(volatile unsigned*)&p.ctr->abort != 0u; };
   const unsigned long long wait_limit = p.wait_ns ? p.wait_ns : kProducerWaitNs;
-  unsigned t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
-  int ends = 0;
-  for (unsigned s = 0;; ++s) {
+  // producer 0: tickets of the pair (2k, 2k + 1), the next pair requested early
+  unsigned pair_next = (pi == 0 && !aborted()) ? atomicAdd(&p.ctr->ticket, 2u) : 0xffffffffu;
+  for (unsigned k = 0;; ++k) {
+    const unsigned s = 2u * k + (unsigned)pi;
     const int b = (int)(s % kStages);
+    uint64_t* full = &full_bar[s % kFullBars];
     unsigned char* buf = stage0 + (size_t)b * p.stage_bytes;
-    const unsigned t = t_next;
+    unsigned t = 0xffffffffu;
+    if (pi == 0) {
+      t = pair_next;
+      ho->tk[k % kTicketQ] = t == 0xffffffffu ? t : t + 1u;
+      __threadfence_block();
+      st_volatile_u32(&ho->tk_stamp[k % kTicketQ], k + 1u);
+    } else {
+      const unsigned long long t0 = global_timer_ns();
+      bool ok = true;
+      while (ld_volatile_u32(&ho->tk_stamp[k % kTicketQ]) != k + 1u) {
+        if (global_timer_ns() - t0 > wait_limit) {
+          give_up();
+          ok = false;
+          break;
+        }
+      }
+      if (ok) {
+        __threadfence_block();
+        t = ho->tk[k % kTicketQ];
+      }
+    }
     int kind = kEndItem, f = 0, item = 0;
-    if (t < total && ends == 0) p.sch.decode(t, kind, f, item);
+    if (t < total && !aborted()) p.sch.decode(t, kind, f, item);
+    const int slot = (p.tab0 + f) % p.nl;
+    // input rows a row item stages (from its rows' y taps): loaded before the
+    // dependency wait so that the two round trips overlap
+    int ylo = 0, yhi = 0;
+    if (kind == kRowItem && !AF) {
+      const Tap* yt = p.ytab + (size_t)slot * NY;
+      ylo = yt[item * RPI].base;
+      yhi = yt[item * RPI + RPI - 1].base;
+    }
     // 1. its dependency: a column item needs every row item of its frame; a row
     //    item needs the columns of the frame whose scratch slot it reuses
     if (kind != kEndItem) {
@@ -394,7 +438,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
       if (dep && ld_acquire_gpu(dep) < target) {
         const unsigned long long t0 = global_timer_ns();
         while (ld_acquire_gpu(dep) < target) {
-          if (*(volatile unsigned*)&p.ctr->abort || global_timer_ns() - t0 > wait_limit) {
+          if (aborted() || global_timer_ns() - t0 > wait_limit) {
             give_up();
             kind = kEndItem;
             break;
@@ -404,12 +448,10 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
       }
     }
     fence_proxy_async_global();  // the acquired data is read by TMA (async proxy)
-    const int slot = (p.tab0 + f) % p.nl;
     Desc d{kind, f, item, 0, 0, slot};
     if (kind == kRowItem && !AF) {
-      const Tap* yt = p.ytab + (size_t)slot * NY;
-      d.jlo = yt[item * RPI].base;
-      d.nrows = yt[item * RPI + RPI - 1].base + 1 - d.jlo + 1;
+      d.jlo = ylo;
+      d.nrows = yhi + 1 - ylo + 1;
     }
     // 2. the buffer's previous hand-over must be published (its consumers done)
     if (s >= (unsigned)kStages && ld_volatile_u32(&ho->published) + kStages <= s) {
@@ -417,7 +459,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
       while (ld_volatile_u32(&ho->published) + kStages <= s) {
         if (global_timer_ns() - t0 > wait_limit) {
           give_up();
-          kind = kEndItem;  // the buffer's old item is lost; the consumers still get end marks
+          kind = kEndItem;  // the buffer's old item is lost; the group still gets its end mark
           break;
         }
       }
@@ -425,9 +467,10 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
     // 3. hand over
     if (kind == kEndItem) {
       desc[b] = Desc{kEndItem, 0, 0, 0, 0, 0};
-      mbar_arrive(&full_bar[b]);
-      if (++ends == kGroups) break;
-      continue;
+      mbar_arrive(full);
+      __threadfence_block();
+      st_volatile_u32(&ho->stamp[s % kPubQ], (s + 1u) | kEndStamp);
+      break;
     }
     ho->kind[s % kPubQ] = kind;
     ho->f[s % kPubQ] = f;
@@ -437,64 +480,59 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
       const int q = af_bin(f, p.nl);
       const int plane = q <= p.nl / 2 ? q : p.nl - q;
       const unsigned bytes = (unsigned)(RPI * NX * sizeof(float2));
-      mbar_arrive_tx(&full_bar[b], bytes);
-      tma_load_1d(buf, p.aplanes + ((size_t)plane * NY + item * RPI) * NX, bytes, &full_bar[b]);
+      mbar_arrive_tx(full, bytes);
+      tma_load_1d(buf, p.aplanes + ((size_t)plane * NY + item * RPI) * NX, bytes, full);
     } else if (kind == kRowItem) {
       const unsigned bytes = (unsigned)(d.nrows * NX * sizeof(uint16_t));
       const unsigned tap_off = (unsigned)row_taps_offset<NX>(d.nrows);
       const unsigned tap_bytes = (unsigned)(NX * sizeof(Tap));
       const unsigned yt_bytes = (unsigned)(RPI * sizeof(Tap));
       const unsigned cy_bytes = (unsigned)(RPI * sizeof(float2));
-      mbar_arrive_tx(&full_bar[b], bytes + tap_bytes + yt_bytes + cy_bytes);
+      mbar_arrive_tx(full, bytes + tap_bytes + yt_bytes + cy_bytes);
       const int fr = (p.ring_start + f) % p.nl;
-      tma_load_1d(buf, p.frames + ((size_t)fr * NY + d.jlo) * NX, bytes, &full_bar[b]);
-      tma_load_1d(buf + tap_off, p.xtab + (size_t)slot * NX, tap_bytes, &full_bar[b]);
-      tma_load_1d(buf + tap_off + tap_bytes, p.ytab + (size_t)slot * NY + item * RPI, yt_bytes, &full_bar[b]);
-      tma_load_1d(buf + tap_off + tap_bytes + yt_bytes, p.cy + item * RPI, cy_bytes, &full_bar[b]);
+      tma_load_1d(buf, p.frames + ((size_t)fr * NY + d.jlo) * NX, bytes, full);
+      tma_load_1d(buf + tap_off, p.xtab + (size_t)slot * NX, tap_bytes, full);
+      tma_load_1d(buf + tap_off + tap_bytes, p.ytab + (size_t)slot * NY + item * RPI, yt_bytes, full);
+      tma_load_1d(buf + tap_off + tap_bytes + yt_bytes, p.cy + item * RPI, cy_bytes, full);
     } else {
-      mbar_arrive_tx(&full_bar[b], (unsigned)(NY * BC * sizeof(float2)));
+      mbar_arrive_tx(full, (unsigned)(NY * BC * sizeof(float2)));
       const int x = 2 * item * BC;
       const int y0 = (f % p.sch.slots) * NY;
 #pragma unroll
       for (int i = 0; i < NY / BOX_ROWS; ++i)
-        tma_load_2d(buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), tmap, x, y0 + i * BOX_ROWS, &full_bar[b]);
+        tma_load_2d(buf + (size_t)i * BOX_ROWS * BC * sizeof(float2), tmap, x, y0 + i * BOX_ROWS, full);
     }
     __threadfence_block();
-    st_volatile_u32(&ho->handed, s + 1);
-    // the next ticket, requested once this one is handed over
-    t_next = *(volatile unsigned*)&p.ctr->abort ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 1u);
+    st_volatile_u32(&ho->stamp[s % kPubQ], s + 1u);
+    if (pi == 0) pair_next = aborted() ? 0xffffffffu : atomicAdd(&p.ctr->ticket, 2u);
   }
-  __threadfence_block();
-  st_volatile_u32(&ho->finished, 1u);
 }
 
-// Publisher warp, one thread: in hand-over order, waits (bounded) until the
-// item's consumers arrive on its buffer's done barrier, then publishes it to
-// other CTAs with a release increment of its frame's counter, which orders the
-// item's outputs (the consumers' stores) before it at GPU scope.
+// Publisher warp, one thread: in hand-over order, waits (bounded) for the
+// position to be handed over and for its consumers to arrive on its buffer's
+// done barrier, then publishes the item to other CTAs with a release increment
+// of its frame's counter, which orders the item's outputs (the consumers'
+// stores) before it at GPU scope.  The first end mark ends it: tickets grow with
+// positions, so no item follows an end mark.
 __device__ void publisher(const LateralParams& p, uint64_t* done_bar, Handover* ho) {
   auto give_up = [&]() {
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
     atomicExch(&p.ctr->abort, 1u);
   };
-  const unsigned long long wait_limit = p.wait_ns ? p.wait_ns : kProducerWaitNs;
+  const unsigned long long wait_limit = 2 * (p.wait_ns ? p.wait_ns : kProducerWaitNs);
   for (unsigned s = 0;; ++s) {
-    if (ld_volatile_u32(&ho->handed) <= s) {
+    unsigned st = ld_volatile_u32(&ho->stamp[s % kPubQ]);
+    if ((st & ~kEndStamp) != s + 1u) {
       const unsigned long long t0 = global_timer_ns();
-      for (;;) {
-        if (ld_volatile_u32(&ho->handed) > s) break;
-        if (ld_volatile_u32(&ho->finished)) {
-          __threadfence_block();
-          if (ld_volatile_u32(&ho->handed) <= s) return;  // everything handed over is published
-          break;
-        }
-        if (global_timer_ns() - t0 > 2 * wait_limit) {
+      while (((st = ld_volatile_u32(&ho->stamp[s % kPubQ])) & ~kEndStamp) != s + 1u) {
+        if (global_timer_ns() - t0 > wait_limit) {
           give_up();
           return;
         }
         __nanosleep(32);
       }
     }
+    if (st & kEndStamp) return;
     __threadfence_block();
     const int kind = ho->kind[s % kPubQ];
     const int f = ho->f[s % kPubQ];
@@ -503,14 +541,14 @@ __device__ void publisher(const LateralParams& p, uint64_t* done_bar, Handover* 
     if (!mbar_test(&done_bar[b], parity)) {
       const unsigned long long t0 = global_timer_ns();
       while (!mbar_test(&done_bar[b], parity)) {
-        if (global_timer_ns() - t0 > 2 * wait_limit) {
+        if (global_timer_ns() - t0 > wait_limit) {
           give_up();
           return;
         }
       }
     }
     red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u);
-    st_volatile_u32(&ho->published, s + 1);
+    st_volatile_u32(&ho->published, s + 1u);
   }
 }
 
@@ -522,20 +560,19 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   static_assert(Split<NX>::N2 % Split<NX>::N1 == 0 && Split<NY>::N2 % Split<NY>::N1 == 0,
                 "the second stage needs N1 | N2");
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t full_bar[kFullBars];
   __shared__ __align__(8) uint64_t done_bar[kStages];
   __shared__ Desc desc[kStages];
   __shared__ Handover ho;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    ho.handed = 0u;
-    ho.finished = 0u;
     ho.published = 0u;
+    for (int i = 0; i < kPubQ; ++i) ho.stamp[i] = 0u;
+    for (int i = 0; i < kTicketQ; ++i) ho.tk_stamp[i] = 0u;
 #pragma unroll
-    for (int b = 0; b < kStages; ++b) {
-      mbar_init(&full_bar[b], 1);
-      mbar_init(&done_bar[b], kThreads);
-    }
+    for (int b = 0; b < kFullBars; ++b) mbar_init(&full_bar[b], 1);
+#pragma unroll
+    for (int b = 0; b < kStages; ++b) mbar_init(&done_bar[b], kThreads);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -544,8 +581,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   float2* twy = twx + NX;
   float2* cxs = twy + NY;
   if (tid >= kGroups * kThreads) {
-    if (tid == kGroups * kThreads) producer<NX, NY, FW, AF>(p, &tmap, full_bar, desc, stage0, &ho);
-    if (tid == kGroups * kThreads + 32) publisher(p, done_bar, &ho);
+    const int w = (tid - kGroups * kThreads) / 32;
+    if (tid % 32 == 0) {
+      if (w < kProducers) producer<NX, NY, FW, AF>(p, &tmap, full_bar, desc, stage0, &ho, w);
+      else publisher(p, done_bar, &ho);
+    }
     return;
   }
   for (int i = tid; i < NX; i += kGroups * kThreads) {
@@ -554,16 +594,17 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   }
   for (int i = tid; i < NY; i += kGroups * kThreads) twy[i] = ldg2(p.twy + i);
   asm volatile("bar.sync 3, %0;" ::"n"(kGroups * kThreads) : "memory");  // tables seen by both groups
-  // Group g takes hand-overs s = g, g + kGroups, ...: buffer s mod kStages, the
-  // (s / kStages)-th fill of that buffer.  The buffer's previous fill (s -
-  // kStages) went to the other group and preceded this group's previous one, so
-  // the parity wait cannot pass early.
+  // Group g takes hand-overs s = g, g + kGroups, ...: buffer s mod kStages, full
+  // barrier s mod kFullBars, whose previous fill (s - kFullBars) this group has
+  // consumed and whose next fill needs this one published, so the parity wait
+  // is exact.
   const int g = tid / kThreads;
   for (unsigned s = g;; s += kGroups) {
     const int b = (int)(s % kStages);
     // consumers wait longer than the producer, which gives up first and hands
     // each group an end mark
-    const bool ok = mbar_wait(&full_bar[b], (s / kStages) & 1u, p.ctr, p.wait_ns ? 2 * p.wait_ns : kConsumerWaitNs);
+    const bool ok = mbar_wait(&full_bar[s % kFullBars], (s / kFullBars) & 1u, p.ctr,
+                              p.wait_ns ? 2 * p.wait_ns : kConsumerWaitNs);
     // the group agrees, and its previous item is finished in all its threads
     if (consumers_sync_or(g, !ok)) break;
     const Desc d = desc[b];

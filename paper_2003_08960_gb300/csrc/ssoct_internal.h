@@ -59,35 +59,40 @@ struct LateralSchedule {
 
   __host__ __device__ long long total() const { return (long long)nl * (n_row + n_col); }
 
-  __host__ __device__ void decode(long long k, int& kind, int& frame, int& item) const {
-    const long long head = (long long)lag * n_row;
+  // 32-bit arithmetic: a sweep has at most 512 x 2 x 1024 tickets, and the
+  // producer decodes one per item, so 64-bit division would cost it hundreds
+  // of cycles.
+  __host__ __device__ void decode(unsigned k, int& kind, int& frame, int& item) const {
+    const unsigned nr = (unsigned)n_row, nc = (unsigned)n_col;
+    const unsigned head = (unsigned)lag * nr;
     if (k < head) {
       kind = 0;
-      frame = (int)(k / n_row);
-      item = (int)(k % n_row);
+      frame = (int)(k / nr);
+      item = (int)(k - (unsigned)frame * nr);
       return;
     }
     k -= head;
-    const long long per = n_row + n_col;
-    const long long both = (long long)(nl - lag) * per;
+    const unsigned per = nr + nc;
+    const unsigned both = (unsigned)(nl - lag) * per;
     if (k < both) {
-      const int step = lag + (int)(k / per);
-      const int r = (int)(k % per);
-      if (r < n_row) {
+      const unsigned st = k / per;
+      const unsigned r = k - st * per;
+      if (r < nr) {
         kind = 0;
-        frame = step;
-        item = r;
+        frame = lag + (int)st;
+        item = (int)r;
       } else {
         kind = 1;
-        frame = step - lag;
-        item = r - n_row;
+        frame = (int)st;
+        item = (int)(r - nr);
       }
       return;
     }
     k -= both;
     kind = 1;
-    frame = nl - lag + (int)(k / n_col);
-    item = (int)(k % n_col);
+    const unsigned q = k / nc;
+    frame = nl - lag + (int)q;
+    item = (int)(k - q * nc);
   }
 };
 
