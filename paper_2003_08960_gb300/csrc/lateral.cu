@@ -554,8 +554,7 @@ __device__ void publisher(const LateralParams& p, uint64_t* done_bar, Handover* 
 
 template <int NX, int NY, bool FW, bool AF>
 __global__ void __launch_bounds__(kCtaThreads, 1)
-    lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap,
-                   const __grid_constant__ CUtensorMap tmap_inter) {
+    lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
   static_assert(Split<NX>::N2 % Split<NX>::N1 == 0 && Split<NY>::N2 % Split<NY>::N1 == 0,
                 "the second stage needs N1 | N2");
@@ -642,8 +641,7 @@ size_t smem_for(const Plan& p) {
 }
 
 template <int NX, int NY, bool FW, bool AF>
-cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, const void* tmap, const void* tmap_inter,
-                      int num_sms, cudaStream_t s) {
+cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, const void* tmap, int num_sms, cudaStream_t s) {
   size_t sb, smem;
   smem_layout<NX, NY>(p, sb, smem);
   LateralParams lp = lp_in;
@@ -658,19 +656,18 @@ cudaError_t launch_fw(const Plan& p, const LateralParams& lp_in, const void* tma
   if (per_sm < 1) per_sm = 1;
   int grid = (num_sms > 0 ? num_sms : 1) * per_sm;
   if (grid > total) grid = (int)total;
-  lateral_kernel<NX, NY, FW, AF><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(tmap),
-                                                                 *reinterpret_cast<const CUtensorMap*>(tmap_inter));
+  lateral_kernel<NX, NY, FW, AF><<<grid, kCtaThreads, smem, s>>>(lp, *reinterpret_cast<const CUtensorMap*>(tmap));
   return cudaGetLastError();
 }
 
 template <int NX, int NY>
-cudaError_t launch(const Plan& p, const LateralParams& lp, const void* tmap, const void* tmap_inter, int num_sms,
+cudaError_t launch(const Plan& p, const LateralParams& lp, const void* tmap, int num_sms,
                    cudaStream_t s) {
   if (p.axial_first)
-    return lateral_full_window(p) ? launch_fw<NX, NY, true, true>(p, lp, tmap, tmap_inter, num_sms, s)
-                                  : launch_fw<NX, NY, false, true>(p, lp, tmap, tmap_inter, num_sms, s);
-  return lateral_full_window(p) ? launch_fw<NX, NY, true, false>(p, lp, tmap, tmap_inter, num_sms, s)
-                                : launch_fw<NX, NY, false, false>(p, lp, tmap, tmap_inter, num_sms, s);
+    return lateral_full_window(p) ? launch_fw<NX, NY, true, true>(p, lp, tmap, num_sms, s)
+                                  : launch_fw<NX, NY, false, true>(p, lp, tmap, num_sms, s);
+  return lateral_full_window(p) ? launch_fw<NX, NY, true, false>(p, lp, tmap, num_sms, s)
+                                : launch_fw<NX, NY, false, false>(p, lp, tmap, num_sms, s);
 }
 
 #define SSOCT_LATERAL_SIZES(X) \
@@ -694,16 +691,16 @@ size_t lateral_smem_bytes(const Plan& p) {
 
 int lateral_col_band(int ny) { return kThreads / split_n1(ny); }
 
-cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap, const void* tmap_inter,
+cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap,
                                 int num_sms, cudaStream_t s) {
-#define X(a, b) if (p.nx == a && p.ny == b) return launch<a, b>(p, lp, tmap, tmap_inter, num_sms, s);
+#define X(a, b) if (p.nx == a && p.ny == b) return launch<a, b>(p, lp, tmap, num_sms, s);
   SSOCT_LATERAL_SIZES(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_lateral(const Plan& p, const LateralParams& lp, cudaStream_t s) {
-  return launch_lateral_with(p, lp, p.tmap, p.tmap_inter, p.num_sms, s);
+  return launch_lateral_with(p, lp, p.tmap, p.num_sms, s);
 }
 
 }  // namespace ssoct

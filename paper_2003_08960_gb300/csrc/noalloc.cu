@@ -106,9 +106,8 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("counter reset: ") + cudaGetErrorString(e));
 
   alignas(64) unsigned char tmap[128];
-  alignas(64) unsigned char tmap_inter[128];
-  if (!encode_scratch_map_at(p, ws + p.off_scratch, tmap) || !encode_inter_map_at(p, ws + p.off_inter, tmap_inter))
-    return fail(p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the no-allocation scratch or intermediate");
+  if (!encode_scratch_map_at(p, ws + p.off_scratch, tmap))
+    return fail(p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the no-allocation scratch ring");
 
   LateralParams lp;
   lp.frames = frames_dev;
@@ -132,7 +131,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   lp.stage_rows = p.stage_rows;
   lp.stage_bytes = 0;
   lp.wait_ns = p.wait_ns;
-  e = launch_lateral_with(p, lp, tmap, tmap_inter, g_num_sms[dev], s);
+  e = launch_lateral_with(p, lp, tmap, g_num_sms[dev], s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("lateral kernel launch: ") + cudaGetErrorString(e));
 
   AxialParams ap;

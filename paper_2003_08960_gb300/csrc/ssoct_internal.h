@@ -196,7 +196,6 @@ struct Plan {
   int device = -1;
   int num_sms = 0;
   alignas(64) unsigned char tmap[128];        // CUtensorMap of the scratch ring (column bands)
-  alignas(64) unsigned char tmap_inter[128];  // CUtensorMap of the sweep-axis intermediate (whole-frame plans)
   // frame ring state
   long long pushed = 0;     // frames in the current gate (capped at nl)
   int ring_head = 0;        // next ring slot to write
@@ -256,10 +255,9 @@ int lateral_col_band(int ny);
 // and a lateral launch that takes the tensor map and SM count explicitly.
 Plan& plan_of(ssoct_plan h);
 bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out);
-bool encode_inter_map_at(const Plan& p, void* inter_dev, void* map_out);
-cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap, const void* tmap_inter,
+cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap,
                                 int num_sms, cudaStream_t s);
-// Whole-frame window: the lateral kernel then writes its outputs with TMA.
+// Whole-frame window: the lateral kernel then needs no window bounds checks.
 inline bool lateral_full_window(const Plan& p) { return p.x0 == 0 && p.y0 == 0 && p.wx == p.nx && p.wy == p.ny; }
 
 }  // namespace ssoct

@@ -151,23 +151,6 @@ bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out) {
   return r == CUDA_SUCCESS;
 }
 
-// Tensor map over the sweep-axis intermediate seen as float32
-// [wy][2 * ntx * nl * 32]; one box is a column item's output (2 * band floats x
-// min(ny, 256) rows).  Only whole-frame plans write it with TMA.
-bool encode_inter_map_at(const Plan& p, void* inter_dev, void* map_out) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
-  const int band = lateral_col_band(p.ny);
-  const cuuint64_t row = (cuuint64_t)p.ntx * p.nl * kTile * 2;  // floats per window row
-  cuuint64_t dims[2] = {row, (cuuint64_t)p.wy};
-  cuuint64_t strides[1] = {row * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)(p.ny < 256 ? p.ny : 256)};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, inter_dev, dims,
-                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
 
 }  // namespace ssoct
 
@@ -396,9 +379,9 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
       p.ws = nullptr;
       return cuda_fail(&p, e, "chirp table upload");
     }
-  } else if (!encode_scratch_map(p) || !encode_inter_map_at(p, p.ws + p.off_inter, p.tmap_inter)) {
+  } else if (!encode_scratch_map(p)) {
     p.ws = nullptr;
-    return fail(&p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the scratch ring or the intermediate");
+    return fail(&p, SSOCT_ECUDA, "cuTensorMapEncodeTiled failed for the scratch ring");
   }
   p.pushed = 0;
   p.ring_head = 0;
