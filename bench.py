@@ -245,10 +245,13 @@ def run_ssoct(args):
     ms, value = aggregate(ms, voxels, world, dist if world > 1 else None, device="cuda")
 
     peak, peak_kind = _peaks()
-    tc = None if (tc_main or args.no_e2e) else _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak)
-    sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if not args.no_e2e else None
-    aberration = _aberration(args, ss, torch, synth, stream) if not args.no_e2e else None
-    batched = _batched(args, ss, torch, synth, w, frames, stream) if not args.no_e2e else None
+    # single-GPU side lines (the N-GPU run keeps the main line and the end-to-end
+    # line, which every rank measures as a replica)
+    extra = not args.no_e2e and world == 1
+    tc = _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak) if extra and not tc_main else None
+    sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if extra else None
+    aberration = _aberration(args, ss, torch, synth, stream) if extra else None
+    batched = _batched(args, ss, torch, synth, w, frames, stream) if extra else None
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
     e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
