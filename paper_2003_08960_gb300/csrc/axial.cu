@@ -10,6 +10,7 @@
 // through shared memory and N1-point DFTs, and stores 128-byte runs of the
 // volume per depth bin.
 #include "fft_common.cuh"
+#include "mbarrier.cuh"
 
 namespace ssoct {
 namespace {
@@ -60,6 +61,152 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_kernel(const __gr
       if (p.cplx) __stcs(p.cplx + (size_t)q * plane + (size_t)kyw * p.wx + kxw, cmul(v, of));
     }
   });
+}
+
+// Streaming form for sweeps of up to 256 frames: one persistent CTA per SM,
+// two consumer groups and a ring of shared-memory stage buffers.  Whole tiles
+// (N_lambda x 32 complex values, contiguous in the intermediate) arrive by 1D
+// TMA bulk copies, a ring's worth ahead; group g computes the CTA's tiles
+// g, g + 2, ... with the same two-stage DFT as axial_kernel, doing the exchange
+// in place in the stage buffer, and once all its threads are done with a
+// buffer one of them issues the copy of the tile kStages further on into it.
+// The loads never wait for the arithmetic, so HBM keeps streaming.
+constexpr int kAxGroups = 2;
+constexpr size_t kAxRingBytes = 192 * 1024;
+constexpr unsigned long long kAxWaitNs = 4000000000ull;  // 4 s
+
+template <int NL>
+struct AxStream {
+  static constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  static constexpr int kGroupThreads = kTile * N1;
+  static constexpr int kThreadsAll = kAxGroups * kGroupThreads;
+  static constexpr size_t kTileBytes = (size_t)NL * kTile * sizeof(float2);
+  static constexpr int kStages = kAxRingBytes / kTileBytes > 8 ? 8 : (int)(kAxRingBytes / kTileBytes);
+  // one full barrier per tile index mod lcm(kStages, kAxGroups): each is waited
+  // on by one group only, which has consumed its previous fill, and its fills
+  // follow one another through the buffer chain t -> t + kStages
+  static constexpr int kFull = kStages % kAxGroups == 0 ? kStages : kStages * kAxGroups;
+};
+
+__device__ bool mbar_wait_bounded(uint64_t* b, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  while (!mbar_try(b, parity))
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+// Barrier of one consumer group (named barrier id, T threads); returns the OR of v.
+template <int T>
+__device__ __forceinline__ bool group_sync_or(int id, bool v) {
+  unsigned r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+               : "=r"(r)
+               : "r"((unsigned)v), "r"(id), "n"(T)
+               : "memory");
+  return r != 0;
+}
+template <int T>
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(T) : "memory");
+}
+
+// Copy of the CTA's tile t (global tile blockIdx.x + t * gridDim.x) into stage
+// buffer t mod kStages; fills[] counts the copies issued on each full barrier.
+template <int NL>
+__device__ __forceinline__ void axial_fill(const AxialParams& p, unsigned char* ring, uint64_t* full_bar,
+                                           unsigned* fills, int t) {
+  using S = AxStream<NL>;
+  const int f = t % S::kFull;
+  atomicAdd(&fills[f], 1u);
+  mbar_arrive_tx(&full_bar[f], (unsigned)S::kTileBytes);
+  const size_t gt = blockIdx.x + (size_t)t * gridDim.x;
+  tma_load_1d(ring + (size_t)(t % S::kStages) * S::kTileBytes, p.inter + gt * NL * kTile, (unsigned)S::kTileBytes,
+              &full_bar[f]);
+}
+
+template <int NL>
+__global__ void __launch_bounds__(AxStream<NL>::kThreadsAll, 1)
+    axial_stream_kernel(const __grid_constant__ AxialParams p) {
+  using S = AxStream<NL>;
+  constexpr int N1 = S::N1, N2 = S::N2, T = S::kGroupThreads;
+  static_assert(N2 % N1 == 0, "the second stage needs N1 | N2");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full_bar[S::kFull];
+  __shared__ unsigned fills[S::kFull];
+  const int tid = threadIdx.x;
+  const int ntiles = p.ntx * p.wy;
+  const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (tid == 0) {
+#pragma unroll
+    for (int b = 0; b < S::kFull; ++b) {
+      mbar_init(&full_bar[b], 1);
+      fills[b] = 0u;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int t = 0; t < S::kStages && t < mine; ++t) axial_fill<NL>(p, smem, full_bar, fills, t);
+  }
+  __syncthreads();
+  const int g = tid / T;
+  const int lt = tid % T;
+  const int pix = lt % kTile;
+  const int j1 = lt / kTile;
+  const size_t plane = (size_t)p.wy * p.wx;
+  for (int i = g, prev = -1;; prev = i, i += kAxGroups) {
+    group_sync<T>(1 + g);  // every thread of the group is done with tile prev's buffer
+    if (lt == 0 && prev >= 0 && prev + S::kStages < mine) axial_fill<NL>(p, smem, full_bar, fills, prev + S::kStages);
+    if (i >= mine) break;
+    const bool ok = mbar_wait_bounded(&full_bar[i % S::kFull], (unsigned)(i / S::kFull) & 1u, kAxWaitNs);
+    if (!ok) atomicOr(p.err, kErrAxial);
+    if (group_sync_or<T>(1 + g, !ok)) break;
+    float2* ex = reinterpret_cast<float2*>(smem + (size_t)(i % S::kStages) * S::kTileBytes);
+    float2 a[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) a[j2] = ex[(j1 + N1 * j2) * kTile + pix];
+    Dft<N2, -1>::template run<1, 0>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], ldg2(p.twl + k2 * N1 + j1));
+    // t = k2 N1 + j1 runs over the same frames j1 + N1 j2 this thread read
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * kTile + pix] = a[k2];
+    // these writes come before the buffer's next TMA fill (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    group_sync<T>(1 + g);
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int ii = decltype(I)::value;
+      const int k2 = j1 + N1 * ii;
+#pragma unroll
+      for (int jj = 0; jj < N1; ++jj) a[ii * N1 + jj] = ex[(k2 * N1 + jj) * kTile + pix];
+      Dft<N1, -1>::template run<1, ii * N1>(a);
+    });
+    const int gt = (int)blockIdx.x + i * (int)gridDim.x;
+    const int kyw = gt / p.ntx;
+    const int kxw = (gt - kyw * p.ntx) * kTile + pix;
+    if (kxw >= p.wx) continue;
+    float* vol = p.vol + (size_t)kyw * p.wx + kxw;
+    float2 of = make_float2(0.f, 0.f);
+    if (p.cplx) of = cmul(ldg2(p.ox + kxw), ldg2(p.oy + kyw));
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int ii = decltype(I)::value;
+      const int k2 = j1 + N1 * ii;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int q = k2 + N2 * k1;
+        const float2 v = a[ii * N1 + k1];
+        float pw = fmaf(v.x, v.x, v.y * v.y) * p.power_scale;
+        if (p.magnitude) pw = sqrtf(pw);
+        __stcs(vol + (size_t)q * plane, pw);
+        if (p.cplx) __stcs(p.cplx + (size_t)q * plane + (size_t)kyw * p.wx + kxw, cmul(v, of));
+      }
+    });
+  }
+  // copies still in flight (after a time-out) write this CTA's shared memory:
+  // they land before it exits.  The last fill of each barrier is its latest
+  // phase, so the parity is exact.
+  __syncthreads();
+  if (tid == 0)
+    for (int f = 0; f < S::kFull; ++f)
+      if (fills[f] && !mbar_wait_bounded(&full_bar[f], (fills[f] - 1u) & 1u, kAxWaitNs)) atomicOr(p.err, kErrAxial);
 }
 
 struct RescaleAxialParams {
@@ -229,7 +376,29 @@ cudaError_t launch_ra(const RescaleAxialParams& rp, cudaStream_t s) {
 }
 
 template <int NL>
-cudaError_t launch(const AxialParams& ap, cudaStream_t s) {
+cudaError_t launch_stream(const AxialParams& ap, int num_sms, cudaStream_t s) {
+  using S = AxStream<NL>;
+  const size_t smem = (size_t)S::kStages * S::kTileBytes;
+  cudaError_t e = cudaFuncSetAttribute(axial_stream_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, axial_stream_kernel<NL>, S::kThreadsAll, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long ntiles = (long long)ap.ntx * ap.wy;
+  long long grid = (long long)(num_sms > 0 ? num_sms : 1) * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) return cudaSuccess;
+  axial_stream_kernel<NL><<<(unsigned)grid, S::kThreadsAll, smem, s>>>(ap);
+  return cudaGetLastError();
+}
+
+template <int NL>
+cudaError_t launch(const AxialParams& ap, int num_sms, cudaStream_t s) {
+  // the streaming form where a tile fits a third of the ring and a group has
+  // eight warps or more; otherwise one CTA per tile
+  constexpr bool kStream = (size_t)NL * kTile * sizeof(float2) <= 64 * 1024 && kTile * split_n1(NL) >= 256;
+  if constexpr (kStream) return launch_stream<NL>(ap, num_sms, s);
   const size_t smem = (size_t)NL * kTile * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(axial_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -292,7 +461,7 @@ bool axial_supported(int nl) {
 }
 
 cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s) {
-#define X(a) if (p.nl == a) return launch<a>(ap, s);
+#define X(a) if (p.nl == a) return launch<a>(ap, p.num_sms, s);
   SSOCT_AXIAL_SIZES(X)
 #undef X
   return cudaErrorInvalidValue;

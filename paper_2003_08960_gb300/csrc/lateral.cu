@@ -29,6 +29,7 @@
 #include <cuda.h>
 
 #include "fft_common.cuh"
+#include "mbarrier.cuh"
 
 namespace ssoct {
 namespace {
@@ -52,39 +53,8 @@ __host__ __device__ __forceinline__ int af_bin(int f, int nl) {
   return (f & 1) ? k : nl - k;
 }
 
-// ---------------------------------------------------------------- mbarrier / TMA
+// ---------------------------------------------------------------- waits
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, unsigned bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 // Bounded wait for an mbarrier phase; on timeout records kErrTimeout and aborts.
 __device__ bool mbar_wait(uint64_t* b, unsigned parity, Counters* c, unsigned long long limit_ns) {
   if (mbar_try(b, parity)) return true;
@@ -98,26 +68,6 @@ __device__ bool mbar_wait(uint64_t* b, unsigned parity, Counters* c, unsigned lo
     }
   }
 }
-// 1D bulk copy global -> shared, completion counted on an mbarrier.
-__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-// 2D tiled tensor copy global -> shared (box as set in the tensor map).
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-// Order generic and async-proxy (TMA) global accesses against each other.
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 // Barrier of consumer group g only (named barrier 1 + g); returns the OR of `v`.
 __device__ __forceinline__ bool consumers_sync_or(int g, bool v) {
   unsigned r;
@@ -255,15 +205,27 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   }
 }
 
+// Row of the band where the first column pass leaves element (j1, k2).  With
+// 64-byte band rows (BC = 8), the second pass's reads of rows jj + N1 k2 for a
+// warp's four consecutive k2 would all fall in the same 16 banks; swapping the
+// row pair (2m, 2m + 1) for odd k2 puts two of them in each half.  The swapped
+// partner row belongs to thread j1 ^ 1 of the same warp.
+template <int N1, int BC>
+__device__ __forceinline__ int col_row(int j1, int k2) {
+  if constexpr (BC == 8) return (j1 ^ (k2 & 1)) + N1 * k2;
+  else return j1 + N1 * k2;
+}
+
 // Column item: window columns [item*BC, item*BC + BC) of frame d.f.  The stage
-// buffer holds the band [NY][BC] copied from the scratch slot; both DFT passes
-// work in place, and whole-frame plans leave the output [NY][BC] there for the
-// producer's tensor store.
+// buffer holds the band [NY][BC] copied from the scratch slot; the first DFT
+// pass writes back in place (up to the row-pair swap of col_row), the second
+// stores the item's outputs straight from registers.
 template <int NY, bool FW, bool AF>
 __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, unsigned char* buf,
                                          const float2* twy, int g) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   constexpr int BC = kThreads / N1;
+  static_assert(BC != 8 || N1 % 2 == 0, "the swapped row pairs lie in one warp");
   const int tid = threadIdx.x % kThreads;
   const int b = tid % BC;
   const int j1 = tid / BC;
@@ -274,14 +236,24 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
   Dft<N2, 1>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], twy[k2 * N1 + j1]);
+  if constexpr (BC == 8) __syncwarp();  // the partner thread has read the rows it will be given
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) tile[(j1 + N1 * k2) * BC + b] = a[k2];  // the rows this thread read
+  for (int k2 = 0; k2 < N2; ++k2) tile[col_row<N1, BC>(j1, k2) * BC + b] = a[k2];
   consumers_sync(g);
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if constexpr (BC == 8) {
+      // row jj ^ sw: jj + sw for even jj, jj - sw for odd jj (two bases, constant offsets)
+      const int sw = k2 & 1;
+      const float2* ev = tile + (N1 * k2 + sw) * BC + b;
+      const float2* od = tile + (N1 * k2 - sw) * BC + b;
 #pragma unroll
-    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = tile[(jj + N1 * k2) * BC + b];
+      for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = (jj & 1) ? od[jj * BC] : ev[jj * BC];
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = tile[(jj + N1 * k2) * BC + b];
+    }
     Dft<N1, 1>::template run<1, i * N1>(a);
   });
   if constexpr (AF) {
@@ -613,6 +585,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
       row_item<NX, NY, FW, AF>(p, d, buf, twx, cxs, g);
     else
       col_item<NY, FW, AF>(p, d, buf, twy, g);
+    // this thread's writes to the buffer come before its next TMA fill (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_arrive(&done_bar[b]);
   }
 }

@@ -144,6 +144,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
   ap.power_scale = (float)(p.alpha * p.alpha);
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
+  ap.err = &lp.ctr->err;
   e = p.use_tc ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb), &lp.ctr->err, s)
                                       : launch_axial(p, ap, s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("axial kernel launch: ") + cudaGetErrorString(e));

@@ -609,6 +609,7 @@ cudaError_t launch_sharpness(const Plan& pl, const uint16_t* frames, float* vol,
     ap.nl = pl.nl; ap.wx = pl.wx; ap.wy = pl.wy; ap.ntx = pl.ntx;
     ap.power_scale = p.alpha2;
     ap.magnitude = 0;
+    ap.err = &((Counters*)(ws + pl.off_ctr))->err;
     e = launch_axial(pl, ap, s);
   }
   const size_t nvox = (size_t)pl.nl * pl.wy * pl.wx;

@@ -42,6 +42,7 @@ struct Counters {
 
 constexpr unsigned kErrTimeout = 1u;      // lateral kernel: a queue wait ran out
 constexpr unsigned kErrAxialTc = 2u;      // tensor-core axial kernel: an MMA wait ran out
+constexpr unsigned kErrAxial = 4u;        // streaming axial kernel: a stage-buffer wait ran out
 
 // Order in which the lateral kernel takes its items.  Step s holds the row
 // items of frame s (if s < nl) and then the column items of frame s - lag (if
@@ -141,6 +142,7 @@ struct AxialParams {
   int nl, wx, wy, ntx;
   float power_scale;       // |K|^2
   int magnitude;           // 1: write |V| instead of |V|^2
+  unsigned* err;           // error word (kErrAxial), the plan's Counters::err
 };
 
 struct CutsParams {

@@ -517,6 +517,7 @@ static ssoct_status launch_axial_pass(Plan& p, float* vol, void* cplx, cudaStrea
   ap.nl = p.nl; ap.wx = p.wx; ap.wy = p.wy; ap.ntx = p.ntx;
   ap.power_scale = (float)(p.alpha * p.alpha);
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
+  ap.err = &((Counters*)(ws + p.off_ctr))->err;
   cudaError_t e = p.use_tc
                       ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb),
                                         &((Counters*)(ws + p.off_ctr))->err, s)
@@ -661,6 +662,7 @@ ssoct_status ssoct_sync(ssoct_plan h, void* stream) {
   if (c.err) {
     cudaMemset(p.ws + p.off_ctr, 0, sizeof(Counters));
     if (c.err & kErrTimeout) return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue");
+    if (c.err & kErrAxial) return fail(&p, SSOCT_ETIMEOUT, "axial kernel gave up waiting on its stage buffers");
     return fail(&p, SSOCT_ETIMEOUT, "tensor-core axial kernel gave up waiting on its MMAs");
   }
   return SSOCT_OK;

@@ -97,6 +97,21 @@ def test_point_scatterer_focus_on_gpu(ss):
         assert min(dq, nl - dq) <= 1, (q, eq)
 
 
+@pytest.mark.parametrize("shape,window", [((64, 64, 256), (5, 3, 37, 11)),      # 22 tiles: fewer than SMs
+                                          ((256, 256, 256), None),               # the 3-buffer ring wraps
+                                          ((128, 128, 128), (7, 9, 100, 70)),    # 6 buffers, ragged tiles
+                                          ((128, 128, 64), None)])               # 8 buffers
+def test_streaming_axial_form(ss, shape, window):
+    """Sweeps of 64 to 256 frames take the persistent axial kernel (TMA-fed ring
+    of stage buffers, two consumer groups): few tiles per SM, many ring wraps
+    and ragged last tiles must all match the oracle, and no wait may run out."""
+    nx, ny, nl = shape
+    w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=5 * nx + ny + nl)
+    plan, vol, cplx, ref = _run(ss, w, window=window, method="fft")
+    _check(vol, cplx, ref, quadrant=window is None)
+    plan.sync()
+
+
 def test_mid_speckle_512(ss):
     w = synth.workload("mid_512x512x128")
     plan, vol, cplx, ref = _run(ss, w, method="fft")
