@@ -326,7 +326,7 @@ struct Handover {
   int kind[kPubQ];
   int f[kPubQ];
   unsigned stamp[kPubQ];     // s + 1 once hand-over s is in place (| kEndStamp for an end mark)
-  unsigned published;        // hand-overs published so far (publisher)
+  unsigned freed;            // hand-overs whose consumers are done with their buffer (publisher)
   unsigned tk[kTicketQ];     // ticket of position 2k + 1, from producer 0 to producer 1
   unsigned tk_stamp[kTicketQ];
 };
@@ -336,12 +336,13 @@ __device__ __forceinline__ void st_volatile_u32(unsigned* a, unsigned v) { *(vol
 
 // Producer warp pi (one thread each), hand-over positions s = 2k + pi.  For
 // each it takes the position's ticket, waits (bounded) for the item's
-// dependency on other CTAs, waits until hand-over s - kStages, the previous user
-// of stage buffer s mod kStages, has been published (so its consumers are
-// done), copies the item's inputs into the buffer with TMA and hands it over to
-// consumer group pi; its last hand-over is that group's end mark.  It publishes
-// nothing: the publisher does, so the release of one item's outputs (a wait for
-// its stores) never delays preparing the next.  Positions follow ticket order
+// dependency on other CTAs, waits until the consumers of hand-over s - kStages,
+// the previous user of stage buffer s mod kStages, are done with it (the
+// publisher's freed count), copies the item's inputs into the buffer with TMA
+// and hands it over to consumer group pi; its last hand-over is that group's
+// end mark.  It publishes nothing: the publisher does, and a buffer is freed
+// before its item is published, so the release of one item's outputs (a wait
+// for its stores, which leave from registers) never delays preparing the next.  Positions follow ticket order
 // and every dependency is on lower tickets, so the queue drains.
 template <int NX, int NY, bool FW, bool AF>
 __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64_t* full_bar, Desc* desc,
@@ -425,10 +426,10 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
       d.jlo = ylo;
       d.nrows = yhi + 1 - ylo + 1;
     }
-    // 2. the buffer's previous hand-over must be published (its consumers done)
-    if (s >= (unsigned)kStages && ld_volatile_u32(&ho->published) + kStages <= s) {
+    // 2. the consumers of the buffer's previous hand-over must be done with it
+    if (s >= (unsigned)kStages && ld_volatile_u32(&ho->freed) + kStages <= s) {
       const unsigned long long t0 = global_timer_ns();
-      while (ld_volatile_u32(&ho->published) + kStages <= s) {
+      while (ld_volatile_u32(&ho->freed) + kStages <= s) {
         if (global_timer_ns() - t0 > wait_limit) {
           give_up();
           kind = kEndItem;  // the buffer's old item is lost; the group still gets its end mark
@@ -482,10 +483,11 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
 
 // Publisher warp, one thread: in hand-over order, waits (bounded) for the
 // position to be handed over and for its consumers to arrive on its buffer's
-// done barrier, then publishes the item to other CTAs with a release increment
-// of its frame's counter, which orders the item's outputs (the consumers'
-// stores) before it at GPU scope.  The first end mark ends it: tickets grow with
-// positions, so no item follows an end mark.
+// done barrier, marks the buffer free for the producers, then publishes the
+// item to other CTAs with a release increment of its frame's counter, which
+// orders the item's outputs (the consumers' stores) before it at GPU scope.
+// The first end mark ends it: tickets grow with positions, so no item follows
+// an end mark.
 __device__ void publisher(const LateralParams& p, uint64_t* done_bar, Handover* ho) {
   auto give_up = [&]() {
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
@@ -519,8 +521,9 @@ __device__ void publisher(const LateralParams& p, uint64_t* done_bar, Handover* 
         }
       }
     }
+    // the buffer can be refilled now: the item's outputs leave from registers
+    st_volatile_u32(&ho->freed, s + 1u);
     red_release_gpu((kind == kRowItem ? p.rows_done : p.cols_done) + f, 1u);
-    st_volatile_u32(&ho->published, s + 1u);
   }
 }
 
@@ -537,7 +540,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   __shared__ Handover ho;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    ho.published = 0u;
+    ho.freed = 0u;
     for (int i = 0; i < kPubQ; ++i) ho.stamp[i] = 0u;
     for (int i = 0; i < kTicketQ; ++i) ho.tk_stamp[i] = 0u;
 #pragma unroll
@@ -567,8 +570,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   asm volatile("bar.sync 3, %0;" ::"n"(kGroups * kThreads) : "memory");  // tables seen by both groups
   // Group g takes hand-overs s = g, g + kGroups, ...: buffer s mod kStages, full
   // barrier s mod kFullBars, whose previous fill (s - kFullBars) this group has
-  // consumed and whose next fill needs this one published, so the parity wait
-  // is exact.
+  // consumed and whose next fill needs this one freed, so the parity wait is
+  // exact.
   const int g = tid / kThreads;
   for (unsigned s = g;; s += kGroups) {
     const int b = (int)(s % kStages);
