@@ -462,7 +462,9 @@ def _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream, step_frames
     return {"step_frames": step_frames, "ms_per_volume": ms, "volumes_per_s": 1000.0 / ms,
             "Gvoxel_per_s": voxels / (ms * 1e-3) / 1e9,
             "cuts_only": {"ms_per_gate": ms_cuts, "gates_per_s": 1000.0 / ms_cuts,
-                          "note": "ssoct_sliding_cuts: xy, xz, yz of each gate, no volume"},
+                          "note": "ssoct_sliding_cuts: xy, xz, yz of each gate, no volume; xy as a running "
+                                  "sum over the gate (new holograms in, replaced ones out), summed in full "
+                                  "again after every nlambda swapped-in frames"},
             "paper": "38 volumes/s (TITAN Xp, sliding 256-frame gate, 512 frames/s)"}
 
 

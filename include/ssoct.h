@@ -226,8 +226,13 @@ SSOCT_API ssoct_status ssoct_sharpness(ssoct_plan plan, const uint16_t* frames_d
  * |V|^2 instead of the volume: xy[wy][wx] at depth bin z0 as one bin of Eq. 7
  * per pixel, xz[nlambda][wx] at row y0 and yz[nlambda][wy] at column x0 (window
  * coordinates) from Eq. 7 on the tiles that hold them.  Any output may be NULL.
- * The cuts equal ssoct_get_cuts of the sliding volume (xz, yz bit for bit; xy
- * to FP32 rounding).  EINVAL if a position lies outside the volume; otherwise as
+ * While z0 stays the same from call to call, the xy cut is a running sum: the
+ * call adds the new frames' holograms and subtracts those they replace (2k
+ * slots read per pixel for k new frames instead of nlambda); after nlambda
+ * frames swapped in, or when z0, the window contents or the plan's other calls
+ * intervene, it is summed over the whole gate again.  The cuts equal
+ * ssoct_get_cuts of the sliding volume (xz, yz bit for bit; xy to FP32
+ * rounding).  EINVAL if a position lies outside the volume; otherwise as
  * ssoct_reconstruct_sliding. */
 SSOCT_API ssoct_status ssoct_sliding_cuts(ssoct_plan plan, int x0, int y0, int z0, float* xy_dev, float* xz_dev,
                                           float* yz_dev, void* stream);

@@ -274,6 +274,7 @@ struct GateCutsParams {
   float* xy;             // [wy][wx] or NULL
   float* xz;             // [nl][wx] or NULL
   float* yz;             // [nl][wy] or NULL
+  float2* xy_state;      // [wy][ntx * 32] X(z0) of the xy cut, or NULL
   int nl, wx, wy, ntx, x0, y0, z0;
   float power_scale;
   int magnitude;
@@ -308,7 +309,52 @@ __global__ void __launch_bounds__(256) gate_xy_kernel(const __grid_constant__ Ga
       k += c.z0;
       if (k >= c.nl) k -= c.nl;
     }
+    if (c.xy_state) c.xy_state[i] = acc;
     if (kxw < c.wx) c.xy[(size_t)kyw * c.wx + kxw] = envelope(acc, c.power_scale, c.magnitude);
+  }
+}
+
+struct XySlideParams {
+  const float2* inter;   // [wy][ntx][nl][32]
+  const float2* wq;      // [nl] exp(-2 pi i k / nl)
+  float2* state;         // [wy][ntx * 32] running X(z0)
+  float* xy;             // [wy][wx] or NULL
+  int nl, wx, wy, ntx, z0, slot0, k;
+  float sign;
+  float power_scale;
+  int magnitude;
+};
+
+// Running xy cut of a sliding gate.  X(z0) = sum_t h_t exp(-2 pi i z0 t / nl)
+// over the gate's slots t is linear in the holograms, so a frame that replaces
+// slot t changes it by (h_new - h_old) exp(-2 pi i z0 t / nl): one pass with
+// sign -1 over the slots about to be overwritten (before the lateral pass) and
+// one with sign +1 after it read k slots per pixel instead of nl.
+__global__ void __launch_bounds__(256) xy_slide_kernel(const __grid_constant__ XySlideParams c) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* w = reinterpret_cast<float2*>(smem);
+  for (int k = threadIdx.x; k < c.nl; k += blockDim.x) w[k] = ldg2(c.wq + k);
+  __syncthreads();
+  const size_t row = (size_t)c.ntx * kTile;
+  const size_t n = (size_t)c.wy * row;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int kyw = (int)(i / row), tile = (int)(i % row) / kTile, pix = (int)(i % kTile);
+    const int kxw = tile * kTile + pix;
+    const float2* h = c.inter + ((size_t)kyw * c.ntx + tile) * c.nl * kTile + pix;
+    float2 d = make_float2(0.f, 0.f);
+    int t = c.slot0;
+    for (int j = 0; j < c.k; ++j) {
+      const float2 v = __ldcs(h + (size_t)t * kTile);
+      const float2 e = w[(c.z0 * t) % c.nl];
+      d.x = fmaf(v.x, e.x, fmaf(-v.y, e.y, d.x));
+      d.y = fmaf(v.x, e.y, fmaf(v.y, e.x, d.y));
+      if (++t == c.nl) t = 0;
+    }
+    float2 acc = c.state[i];
+    acc.x = fmaf(c.sign, d.x, acc.x);
+    acc.y = fmaf(c.sign, d.y, acc.y);
+    c.state[i] = acc;
+    if (c.xy && kxw < c.wx) c.xy[(size_t)kyw * c.wx + kxw] = envelope(acc, c.power_scale, c.magnitude);
   }
 }
 
@@ -411,7 +457,23 @@ cudaError_t launch(const AxialParams& ap, int num_sms, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, float* xz, float* yz, cudaStream_t s) {
+cudaError_t launch_xy_slide(const Plan& p, int slot0, int k, int z0, float sign, float* xy, cudaStream_t s) {
+  XySlideParams c;
+  c.inter = (const float2*)(p.ws + p.off_inter);
+  c.wq = (const float2*)(p.ws + p.off_wq);
+  c.state = (float2*)(p.ws + p.off_xys);
+  c.xy = xy;
+  c.nl = p.nl; c.wx = p.wx; c.wy = p.wy; c.ntx = p.ntx;
+  c.z0 = z0; c.slot0 = slot0; c.k = k;
+  c.sign = sign;
+  c.power_scale = (float)(p.alpha * p.alpha);
+  c.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
+  xy_slide_kernel<<<4 * p.num_sms, 256, (size_t)p.nl * sizeof(float2), s>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, float* xz, float* yz,
+                             float2* xy_state, cudaStream_t s) {
   GateCutsParams c;
   c.inter = (const float2*)(p.ws + p.off_inter);
   c.wq = (const float2*)(p.ws + p.off_wq);
@@ -419,6 +481,7 @@ cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, f
   c.xy = xy;
   c.xz = xz;
   c.yz = yz;
+  c.xy_state = xy_state;
   c.nl = p.nl; c.wx = p.wx; c.wy = p.wy; c.ntx = p.ntx;
   c.x0 = x0; c.y0 = y0; c.z0 = z0;
   c.power_scale = (float)(p.alpha * p.alpha);

@@ -204,6 +204,14 @@ struct Plan {
   long long next_seq = -1;
   long long stream_count = 0;  // frames pushed since the gate (re)started, uncapped
   long long lat_upto = -1;     // sliding gates: stream index up to which the intermediate holds holograms
+  // cuts-only sliding gates: running one-bin transform X(z0) of the gate, valid
+  // for the intermediate as it stood at lat_upto == xs_lat; xs_updates frames
+  // have been swapped in since it was last summed in full
+  size_t off_xys = 0;          // [wy][ntx * 32] complex
+  bool xs_valid = false;
+  int xs_z0 = 0;
+  int xs_updates = 0;
+  long long xs_lat = -1;
   std::string last_error;
   // failure injection (ssoct_inject_stall)
   unsigned inject_skip = 0;
@@ -220,7 +228,13 @@ cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s);
 cudaError_t launch_cuts(const CutsParams& cp, cudaStream_t s);
 // The three cuts of the current gate straight from the sweep-axis intermediate
 // (xy: one bin per pixel; xz, yz: the axial transform of the cut's tiles).
-cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, float* xz, float* yz, cudaStream_t s);
+// xy_state, if not NULL, receives the xy cut's complex X(z0) ([wy][ntx * 32]).
+cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, float* xz, float* yz,
+                             float2* xy_state, cudaStream_t s);
+// Running xy cut of the sliding gate (one bin of Eq. 7 is linear in the gate's
+// holograms): X(z0) += sign * sum over slots slot0 .. slot0 + k - 1 (mod nl) of
+// h_t exp(-2 pi i z0 t / nl), then xy = envelope of X if xy is not NULL.
+cudaError_t launch_xy_slide(const Plan& p, int slot0, int k, int z0, float sign, float* xy, cudaStream_t s);
 // Axial-first order, first pass: Eq. 5 resample of every frame and Eq. 7 over
 // the sweep at every pixel, bins 0..nl/2 written as planes [nl/2 + 1][ny][nx].
 cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring_start, float2* planes,

@@ -302,6 +302,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
   if (generic) p.off_cg = take(sizeof(float2) * (size_t)nx * ny);
   if (p.axial_first) p.off_aplanes = take(sizeof(float2) * (size_t)(nlambda / 2 + 1) * ny * nx);
+  if (!generic && !p.axial_first) p.off_xys = take(sizeof(float2) * (size_t)p.wy * p.ntx * kTile);
   if (generic || (flags & SSOCT_FLAG_PUPIL)) p.off_F = take(sizeof(float2) * (size_t)nlambda * ny * nx);
   if (flags & SSOCT_FLAG_PUPIL) {
     const size_t chunks = (size_t)(nlambda + p.sh_tpc - 1) / p.sh_tpc;
@@ -627,11 +628,47 @@ ssoct_status ssoct_sliding_cuts(ssoct_plan h, int x0, int y0, int z0, float* xy,
   if (x0 < 0 || x0 >= p.wx || y0 < 0 || y0 >= p.wy || z0 < 0 || z0 >= p.nl)
     return fail(&p, SSOCT_EINVAL, "cut position outside the volume");
   cudaStream_t s = (cudaStream_t)stream;
+  // The xy cut is kept as a running sum X(z0) over the gate's slots while z0
+  // stays put: the frames this call swaps in change it by their holograms minus
+  // those they replace.  Once nl frames have been swapped in since the last
+  // full sum, the next call sums the whole gate again, which bounds the
+  // rounding the running sum collects to that of one full sum.
+  bool incremental = false;
+  int slot0 = 0, k = 0;
+  if (xy && p.ws && !p.generic && !p.axial_first && p.stream_count >= p.nl) {
+    const long long first = std::max(p.lat_upto, p.stream_count - p.nl);
+    k = (int)(p.stream_count - first);
+    slot0 = (int)(first % p.nl);
+    incremental = p.xs_valid && p.xs_z0 == z0 && p.xs_lat == p.lat_upto && k < p.nl && p.xs_updates + k <= p.nl;
+  }
+  cudaError_t e = cudaSuccess;
+  if (incremental && k > 0) {
+    e = launch_xy_slide(p, slot0, k, z0, -1.f, nullptr, s);  // the holograms about to be replaced
+    if (e != cudaSuccess) {
+      p.xs_valid = false;
+      return cuda_fail(&p, e, "running xy cut");
+    }
+  }
   cudaEvent_t* ev = nullptr;
   ssoct_status st = sliding_update(p, s, &ev);
-  if (st != SSOCT_OK) return st;
-  const cudaError_t e = launch_gate_cuts(p, x0, y0, z0, xy, xz, yz, s);
-  if (e != cudaSuccess) return cuda_fail(&p, e, "gate cuts kernels");
+  if (st != SSOCT_OK) {
+    p.xs_valid = false;
+    return st;
+  }
+  if (incremental) e = launch_xy_slide(p, slot0, k, z0, 1.f, xy, s);
+  if (e == cudaSuccess)
+    e = launch_gate_cuts(p, x0, y0, z0, incremental ? nullptr : xy, xz, yz,
+                         incremental || !xy ? nullptr : (float2*)(p.ws + p.off_xys), s);
+  if (e != cudaSuccess) {
+    p.xs_valid = false;
+    return cuda_fail(&p, e, "gate cuts kernels");
+  }
+  if (xy) {
+    p.xs_valid = true;
+    p.xs_z0 = z0;
+    p.xs_lat = p.lat_upto;
+    p.xs_updates = incremental ? p.xs_updates + k : 0;
+  }
   if (ev) cudaEventRecord(ev[2], s);
   return SSOCT_OK;
 }

@@ -403,3 +403,45 @@ def test_sliding_cuts_only(ss):
         assert torch.allclose(xy, xy_ref, rtol=1e-4, atol=1e-6 * float(xy_ref.max()))
     with pytest.raises(ss.SsoctError):
         cuts.sliding_cuts(50, 0, 0)
+
+
+def test_sliding_cuts_running_xy(ss):
+    """The running xy cut of cuts-only sliding gates (the new frames' holograms
+    added, the replaced ones subtracted, while z0 stays) against the oracle's
+    |V|^2 plane of each gate: the full re-sum after nlambda swapped-in frames, a
+    change of z0, a call without xy and a full reconstruct in between all come
+    up in the sequence."""
+    ws = [synth.workload("tiny_64x64x32", seed=sd) for sd in (3, 5, 9, 13)]
+    a = ws[0]
+    nl = a.nlambda
+    stream = np.concatenate([w.frames for w in ws])
+    win = (6, 10, 50, 37)
+    plan = ss.Plan(a.nx, a.ny, a.nlambda, a.pitch, a.z, a.lambdas, window=win)
+    cuda_stream = torch.cuda.current_stream().cuda_stream
+    # (new frames, z0, what else happens before the call)
+    seq = [(32, 5, None), (3, 5, None), (7, 5, None), (1, 5, None), (0, 5, None), (13, 5, None),
+           (9, 5, None),                       # 33 frames swapped in since the full sum: re-sum
+           (6, 21, None), (11, 21, None), (4, 21, None),
+           (5, 21, "no-xy"), (8, 21, None),    # a call without xy leaves the running sum stale
+           (10, 21, "full"), (12, 21, None), (2, 21, None)]
+    pushed = 0
+    for step, z0, event in seq:
+        if step:
+            assert plan.push(_dev(stream[pushed:pushed + step])) == ss.SSOCT_OK
+            pushed += step
+        if event == "full":
+            plan.reconstruct(_dev(a.frames))
+        if event == "no-xy":
+            xz = torch.empty((nl, win[2]), dtype=torch.float32, device="cuda")
+            assert ss.ssoct_sliding_cuts(plan.handle, 1, 2, z0, 0, xz.data_ptr(), 0, cuda_stream) == ss.SSOCT_OK
+            plan.sync()
+            continue
+        xy, xz, yz = plan.sliding_cuts(3, 4, z0)
+        plan.sync()
+        gate = stream[pushed - nl:pushed]
+        ref = oracle.reconstruct(np.roll(gate, (pushed - nl) % nl, axis=0), a.pitch, a.z, a.lambdas,
+                                 window=win, method="fft")
+        p_ref = oracle.intensity(ref)
+        err = _rel(xy.cpu().numpy().astype(np.float64), p_ref[z0])
+        assert err <= 2 * TOL, f"xy after {pushed} frames (z0 {z0}): rel L2 {err:.3e}"
+        assert _rel(xz.cpu().numpy().astype(np.float64), p_ref[:, 4, :]) <= 2 * TOL
