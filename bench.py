@@ -272,7 +272,9 @@ def run_ssoct(args):
     for k in kernels.values():
         k["frac"] = k["GBps"] / peak
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    traffic = _traffic("axial_tc" if (tc_main and dom == "axial") else dom)
+    # the stored counters belong to the paper-order kernels at the 1024x1024x256 workload
+    traffic = (_traffic("axial_tc" if (tc_main and dom == "axial") else dom)
+               if not args.axial_first and args.size is None else None)
     whole_bytes = lat_bytes + ax_bytes
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
