@@ -255,6 +255,8 @@ def run_ssoct(args):
 
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
     e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
+    # library-free comparison, last so that its buffers do not touch the lines above
+    cufft = _cufft_chain(torch, frames, nl, w.ny, w.nx, voxels) if extra and not tc_main else None
     if args.axial_first:
         # rescale-axial pass: uint16 frames in, half-spectrum planes out; lateral
         # pass: the planes in (each read once from HBM, its conjugate use from L2),
@@ -301,6 +303,7 @@ def run_ssoct(args):
         "tc_axial": tc,
         "aberration": aberration,
         "batched": batched,
+        "cufft_comparison": cufft,
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
@@ -509,6 +512,59 @@ def _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak):
             "axial_frac": ax_bytes / (ax_ms * 1e-3) / 1e9 / peak,
             "rel_l2_vs_fp32_volume": float(d),
             "form": "axial DFT as two 16-point tcgen05 MMA stages, bf16 hi+lo operands, fp32 accumulate in TMEM"}
+
+
+def _cufft_chain(torch, frames, nl, ny, nx, voxels, steps=10):
+    """Timing comparison only, outside the library: the same step's transforms
+    done with cuFFT through torch.fft on the same GPU.  uint16 frames to complex
+    times a unit-modulus chirp, the 2D DFT of every frame with the + sign of
+    Eq. 6 (unnormalised), the DFT over the sweep (Eq. 7), |.|^2.  The Eq. 5
+    resample has no matching library call and is left out, so the chain does
+    less than the library's step."""
+    f = frames.view(nl, ny, nx)
+    phase = torch.rand((ny, nx), device="cuda", dtype=torch.float32) * 6.283185307179586
+    chirp = torch.polar(torch.ones_like(phase), phase)
+    h = torch.empty((nl, ny, nx), dtype=torch.complex64, device="cuda")
+    g = torch.empty_like(h)
+    p = torch.empty((nl, ny, nx), dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    acc = [0.0, 0.0, 0.0, 0.0]
+
+    def step(timed):
+        if timed:
+            ev[0].record()
+        torch.mul(f.float(), chirp, out=h)                    # frames x chirp
+        if timed:
+            ev[1].record()
+        torch.fft.ifft2(h, norm="forward", out=g)            # + sign, unnormalised (Eq. 6)
+        if timed:
+            ev[2].record()
+        torch.fft.fft(g, dim=0, out=h)                       # over the sweep (Eq. 7)
+        if timed:
+            ev[3].record()
+        torch.abs(h, out=p)
+        p.square_()
+        if timed:
+            ev[4].record()
+            torch.cuda.synchronize()
+            for i in range(4):
+                acc[i] += ev[i].elapsed_time(ev[i + 1])
+
+    for _ in range(3):
+        step(False)
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        step(True)
+    stages = [a / steps for a in acc]
+    ms = sum(stages)
+    out = {"ms_per_step": ms, "Gvoxel_per_s": voxels / (ms * 1e-3) / 1e9,
+           "stages_ms": {"frames_x_chirp": stages[0], "fft2_cufft": stages[1], "fft_sweep_cufft": stages[2],
+                         "abs2": stages[3]},
+           "note": "timing comparison only (torch.fft = cuFFT), not part of the library; without the Eq. 5 "
+                   "resample, full frames (no crop)"}
+    del h, g, p
+    torch.cuda.empty_cache()
+    return out
 
 
 def _aberration(args, ss, torch, synth, stream, steps=10):
