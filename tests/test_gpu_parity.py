@@ -110,6 +110,11 @@ def test_streaming_axial_form(ss, shape, window):
     plan, vol, cplx, ref = _run(ss, w, window=window, method="fft")
     _check(vol, cplx, ref, quadrant=window is None)
     plan.sync()
+    # the |V| envelope from the same kernel
+    mag = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, window=window, flags=ss.SSOCT_FLAG_MAGNITUDE)
+    m = mag.reconstruct(_dev(w.frames)).cpu().numpy().astype(np.float64)
+    mag.sync()
+    assert _rel(m * m, vol.astype(np.float64)) <= 1e-6
 
 
 def test_mid_speckle_512(ss):
