@@ -138,6 +138,46 @@ class Gen:
             self.emit(f"const float2 {v} = make_float2({a}.y, -{a}.x);")
         return v
 
+    def fma2(self, a, c, b):
+        """b + c * a for a real constant c (two FMAs)."""
+        v = self.var()
+        cs = f32(c)
+        self.emit(f"const float2 {v} = make_float2(fmaf({a}.x, {cs}, {b}.x), fmaf({a}.y, {cs}, {b}.y));")
+        return v
+
+    def rot(self, a, k, n, sign):
+        """a * exp(sign 2 pi i k / n) as (r, c) with the product equal to c * r.
+        W = C + iS is written C (1 + i S/C) when |C| >= |S|, else S (C/S + i),
+        so r costs two FMAs (or nothing / two additions for the trivial
+        twiddles) and |c| >= 1/sqrt 2; the scale c is folded into the FMAs of
+        the butterflies that use the product."""
+        k %= n
+        if k == 0:
+            return a, 1.0
+        g = math.gcd(k, n)
+        kk, nn = k // g, n // g
+        if nn == 2:
+            return a, -1.0
+        if nn == 4:
+            return self.mul_i(a, sign if kk == 1 else -sign), 1.0
+        ang = 2 * math.pi * kk / nn
+        C, S = math.cos(ang), sign * math.sin(ang)
+        v = self.var()
+        if nn == 8:
+            # (+-1 +- i) / sqrt 2: r = a (C' + i S') with C', S' = +-1, two additions
+            cx, sx = (1 if C > 0 else -1), (1 if S > 0 else -1)
+            re = f"{'' if cx > 0 else '-'}{a}.x {'-' if sx > 0 else '+'} {a}.y"
+            im = f"{'' if cx > 0 else '-'}{a}.y {'+' if sx > 0 else '-'} {a}.x"
+            self.emit(f"const float2 {v} = make_float2({re}, {im});")
+            return v, math.sqrt(0.5)
+        if abs(C) >= abs(S):
+            t = f32(S / C)
+            self.emit(f"const float2 {v} = make_float2(fmaf(-{a}.y, {t}, {a}.x), fmaf({a}.x, {t}, {a}.y));")
+            return v, C
+        t = f32(C / S)
+        self.emit(f"const float2 {v} = make_float2(fmaf({a}.x, {t}, -{a}.y), fmaf({a}.y, {t}, {a}.x));")
+        return v, S
+
     def split_radix(self, xs, sign):
         """Split-radix decimation in time (Duhamel and Hollmann, 1984), n a power
         of two >= 4: U = DFT_{n/2} of the even samples, Z and Z' = DFT_{n/4} of
@@ -145,7 +185,11 @@ class Gen:
         t1 = W^k Z[k], t2 = W^{3k} Z'[k], s = t1 + t2, d = t1 - t2:
             X[k]        = U[k] + s          X[k + n/2]  = U[k] - s
             X[k + n/4]  = U[k + n/4] + sign i d
-            X[k + 3n/4] = U[k + n/4] - sign i d        (k = 0 .. n/4 - 1)."""
+            X[k + 3n/4] = U[k + n/4] - sign i d        (k = 0 .. n/4 - 1).
+        The twiddle products are kept scaled (t1 = c1 r1, t2 = c3 r3), so that
+        s = c1 (r1 + (c3/c1) r3) and the outputs are fused multiply-adds with
+        c1: four FMAs per twiddle pair instead of the multiplications of the
+        plain form."""
         n = len(xs)
         u = self.dft(xs[0::2], sign)
         z1 = self.dft(xs[1::4], sign)
@@ -153,14 +197,25 @@ class Gen:
         out = [None] * n
         q = n // 4
         for k in range(q):
-            t1 = self.twiddle(z1[k], k, n, sign)
-            t2 = self.twiddle(z3[k], 3 * k, n, sign)
-            sm = self.add(t1, t2)
-            df = self.mul_i(self.sub(t1, t2), sign)
-            out[k] = self.add(u[k], sm)
-            out[k + 2 * q] = self.sub(u[k], sm)
-            out[k + q] = self.add(u[k + q], df)
-            out[k + 3 * q] = self.sub(u[k + q], df)
+            r1, c1 = self.rot(z1[k], k, n, sign)
+            r3, c3 = self.rot(z3[k], 3 * k, n, sign)
+            rho = c3 / c1
+            if abs(rho - 1.0) < 1e-12:
+                sm, df = self.add(r1, r3), self.sub(r1, r3)
+            elif abs(rho + 1.0) < 1e-12:
+                sm, df = self.sub(r1, r3), self.add(r1, r3)
+            else:
+                sm, df = self.fma2(r3, rho, r1), self.fma2(r3, -rho, r1)
+            df = self.mul_i(df, sign)
+            if abs(c1 - 1.0) < 1e-12:
+                out[k], out[k + 2 * q] = self.add(u[k], sm), self.sub(u[k], sm)
+                out[k + q], out[k + 3 * q] = self.add(u[k + q], df), self.sub(u[k + q], df)
+            elif abs(c1 + 1.0) < 1e-12:
+                out[k], out[k + 2 * q] = self.sub(u[k], sm), self.add(u[k], sm)
+                out[k + q], out[k + 3 * q] = self.sub(u[k + q], df), self.add(u[k + q], df)
+            else:
+                out[k], out[k + 2 * q] = self.fma2(sm, c1, u[k]), self.fma2(sm, -c1, u[k])
+                out[k + q], out[k + 3 * q] = self.fma2(df, c1, u[k + q]), self.fma2(df, -c1, u[k + q])
         return out
 
     def dft3(self, xs, sign):
