@@ -647,19 +647,30 @@ def _batched(args, ss, torch, synth, w_1024, frames_1024, stream, steps=10):
                     "384/640/768 frames take the two-pass lateral path"}
 
 
+# sources every kernel is built from besides its own .cu file
+_COMMON_SOURCES = ("fft_codelets.cuh", "fft_common.cuh", "mbarrier.cuh", "ssoct_internal.h")
+
+
+def kernel_source_hash(source: str) -> str:
+    """sha256 (16 hex digits) over a kernel's .cu file and the headers every
+    kernel includes, in a fixed order."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in (source,) + _COMMON_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2003_08960_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _traffic(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel source (null otherwise)."""
-    import hashlib
+    current kernel sources (null otherwise)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
     if not d:
         return None
-    src = os.path.join(ROOT, "paper_2003_08960_gb300", "csrc", d["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return d["bytes_per_launch"] if h == d["source_sha256_16"] else None
+    return d["bytes_per_launch"] if kernel_source_hash(d["source"]) == d["source_sha256_16"] else None
 
 
 def main():
