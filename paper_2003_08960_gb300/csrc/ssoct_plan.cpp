@@ -698,6 +698,10 @@ ssoct_status ssoct_sync(ssoct_plan h, void* stream) {
   if (e != cudaSuccess) return cuda_fail(&p, e, "error word read");
   if (c.err) {
     cudaMemset(p.ws + p.off_ctr, 0, sizeof(Counters));
+    // a kernel gave up part way: the intermediate and the running xy cut no
+    // longer describe the gate, so the next sliding call starts over
+    p.lat_upto = -1;
+    p.xs_valid = false;
     if (c.err & kErrTimeout) return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue");
     if (c.err & kErrAxial) return fail(&p, SSOCT_ETIMEOUT, "axial kernel gave up waiting on its stage buffers");
     return fail(&p, SSOCT_ETIMEOUT, "tensor-core axial kernel gave up waiting on its MMAs");
