@@ -131,6 +131,21 @@ def oracle_rate(w, n_frames: int):
     return w.nx * w.ny * n_frames / dt, dt, os.cpu_count()
 
 
+def oracle_rate_single_core(w, budget_s: float = 8.0):
+    """The same oracle with scipy.fft held to one thread, on a smaller sample:
+    returns (voxels per second, frames, seconds)."""
+    import oracle.ssoct_oracle as so
+    old = so.WORKERS
+    so.WORKERS = 1
+    try:
+        rate, dt, _ = oracle_rate(w, 2)
+        n = int(max(2, min(w.nlambda, budget_s / (dt / 2.0))))
+        rate, dt, _ = oracle_rate(w, n)
+    finally:
+        so.WORKERS = old
+    return rate, n, dt
+
+
 def _sample_frames(w, budget_s: float) -> int:
     rate, dt, _ = oracle_rate(w, 2)
     per_frame = dt / 2.0
@@ -312,6 +327,10 @@ def run_ssoct(args):
         rate, dt, cores = oracle_rate(w, n)
         out["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"FP64 oracle on the first {n} frames ({w.nx}x{w.ny}x{n} gate), {dt:.1f} s"}
+        r1, n1, dt1 = oracle_rate_single_core(w)
+        out["cpu_baseline"]["single_core"] = {
+            "value": r1 / 1e9, "unit": UNIT, "cores": 1,
+            "sample": f"the same oracle with scipy.fft on one thread, first {n1} frames, {dt1:.1f} s"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -38,6 +38,15 @@ import scipy.fft as sfft
 # closed forms (Eq. 3, Eq. 4, z_b)
 # ----------------------------------------------------------------------------
 
+# Threads scipy.fft may use (None: all host cores).  Only the timing of the
+# oracle changes with it, never a value.
+WORKERS = None
+
+
+def _workers() -> int:
+    return WORKERS or os.cpu_count()
+
+
 def start_wavelength(lambdas: Sequence[float]) -> float:
     """lambda_1: the wavelength of the first frame of the sweep (Eq. 5, Eq. 6)."""
     return float(lambdas[0])
@@ -162,7 +171,7 @@ def fresnel(ip: np.ndarray, pitch: float, z: float, lambda1: float, method: str 
     elif method == "fft":
         if nx % 2 or ny % 2:
             raise ValueError("fft method needs even sizes")
-        s = sfft.fftshift(sfft.ifft2(sfft.ifftshift(a), workers=os.cpu_count()))
+        s = sfft.fftshift(sfft.ifft2(sfft.ifftshift(a), workers=_workers()))
         s = s[rows, cols] * (nx * ny)
     else:
         raise ValueError(method)
@@ -182,7 +191,7 @@ def axial(h: np.ndarray, method: str = "dense") -> np.ndarray:
         w = np.exp(-2j * np.pi * np.outer(t, t) / n)
         return (w @ h.reshape(n, -1)).reshape(h.shape)
     if method == "fft":
-        return sfft.fft(h, axis=0, workers=os.cpu_count())
+        return sfft.fft(h, axis=0, workers=_workers())
     raise ValueError(method)
 
 
