@@ -115,8 +115,11 @@ __device__ __forceinline__ int xswz(int k2, int j1) {
   return k2 * N1 + (j1 ^ (k2 & (N1 - 1)));
 }
 
+// Exact (every uint16 is a float).  One conversion instruction: the kernel is
+// bound by instruction issue, and the two-instruction form (OR into the
+// mantissa of 2^23, subtract 2^23) measured 1.5-2 % slower overall.
 __device__ __forceinline__ float u16_to_f(unsigned short u) {
-  return __int_as_float(0x4B000000 | (unsigned)u) - 8388608.0f;  // 2^23 + u, exact
+  return __uint2float_rn((unsigned)u);
 }
 
 // Row item: rows [item*RPI, item*RPI + RPI) of frame d.f.  The stage buffer holds
