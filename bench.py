@@ -263,13 +263,15 @@ def run_ssoct(args):
     # single-GPU side lines (the N-GPU run keeps the main line and the end-to-end
     # line, which every rank measures as a replica)
     extra = not args.no_e2e and world == 1
+    # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to
+    # pinned host (D2H); first of the extra lines, before the others fill the
+    # device with their plans and graphs
+    e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
     tc = _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak) if extra and not tc_main else None
     sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if extra else None
     aberration = _aberration(args, ss, torch, synth, stream) if extra else None
     batched = _batched(args, ss, torch, synth, w, frames, stream) if extra else None
 
-    # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to pinned host (D2H)
-    e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
     # library-free comparison, last so that its buffers do not touch the lines above
     cufft = _cufft_chain(torch, frames, nl, w.ny, w.nx, voxels) if extra and not tc_main else None
     if args.axial_first:
