@@ -450,3 +450,14 @@ def test_sliding_cuts_running_xy(ss):
         err = _rel(xy.cpu().numpy().astype(np.float64), p_ref[z0])
         assert err <= 2 * TOL, f"xy after {pushed} frames (z0 {z0}): rel L2 {err:.3e}"
         assert _rel(xz.cpu().numpy().astype(np.float64), p_ref[:, 4, :]) <= 2 * TOL
+    # the running sum also feeds the |V| envelope
+    mag = ss.Plan(a.nx, a.ny, a.nlambda, a.pitch, a.z, a.lambdas, window=win, flags=ss.SSOCT_FLAG_MAGNITUDE)
+    assert mag.push(_dev(stream[:nl])) == ss.SSOCT_OK
+    mag.sliding_cuts(3, 4, 9)
+    assert mag.push(_dev(stream[nl:nl + 7])) == ss.SSOCT_OK
+    xy, _, _ = mag.sliding_cuts(3, 4, 9)               # running: 7 frames swapped in
+    mag.sync()
+    gate = stream[7:nl + 7]
+    ref = oracle.reconstruct(np.roll(gate, 7 % nl, axis=0), a.pitch, a.z, a.lambdas, window=win, method="fft")
+    err = _rel(xy.cpu().numpy().astype(np.float64), np.sqrt(oracle.intensity(ref)[9]))
+    assert err <= 2 * TOL, f"running |V| xy: rel L2 {err:.3e}"

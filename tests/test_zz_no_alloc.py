@@ -64,14 +64,18 @@ def test_noalloc_matches_workspace_path_on_consecutive_calls(ss):
     import synth
     a = _case(ss, synth.workload("tiny_64x64x32"), None)
     b = _case(ss, synth.workload("custom", nx=128, ny=128, nlambda=16, kind="points", seed=12), (20, 36, 77, 50))
+    # 128 frames: the persistent, TMA-fed axial kernel, its error word in the array
+    c = _case(ss, synth.workload("custom", nx=64, ny=64, nlambda=128, kind="points", seed=13), (3, 5, 57, 41))
     try:
         _call(ss, a)
         _call(ss, a)   # two calls in a row on the same plan
         _call(ss, b)   # a different size and a ragged window over the same array
+        _call(ss, c)
         _call(ss, a)   # and back
     finally:
         ss.ssoct_destroy_plan(a["h"])
         ss.ssoct_destroy_plan(b["h"])
+        ss.ssoct_destroy_plan(c["h"])
 
 
 def test_noalloc_rejects_plans_beyond_its_array(ss):
