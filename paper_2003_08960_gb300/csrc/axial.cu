@@ -4,11 +4,13 @@
 // [q][y][x].  Optionally also V itself with the Eq. 6 prefactor and output
 // chirp applied (unit-modulus factors apart from |K|, so |V|^2 needs only |K|^2).
 //
-// One CTA per 32-pixel tile of one window row: it streams the tile's
-// N_lambda x 32 complex values (contiguous in the intermediate), runs the
+// The unit of work is a 32-pixel tile of one window row: its N_lambda x 32
+// complex values (contiguous in the intermediate) go through the
 // N_lambda-point DFT as N2-point DFTs in registers, a twiddle, an exchange
-// through shared memory and N1-point DFTs, and stores 128-byte runs of the
-// volume per depth bin.
+// through shared memory and N1-point DFTs, and leave as 128-byte runs of the
+// volume per depth bin.  Sweeps of 64 to 256 frames take the persistent
+// streaming form (axial_stream_kernel: TMA-fed ring of stage buffers, two
+// consumer groups per SM); the others one CTA per tile (axial_kernel).
 #include "fft_common.cuh"
 #include "mbarrier.cuh"
 

@@ -8,13 +8,14 @@
 // Memory Accelerator (1D bulk copies of the uint16 input rows and tap tables,
 // or 2D tensor copies of an L2 scratch column band), handing the item over
 // through an mbarrier; producer g feeds consumer group g, hand-overs alternate
-// between them, and two items are computed at once.  Consumers compute in place in the
-// stage buffer, store the item's outputs themselves and arrive on a second
-// mbarrier; the publisher then makes the outputs visible to the other CTAs
-// (release increment of the frame's counter), off the producer's path.
+// between them, and two items are computed at once.  Consumers compute in
+// place in the stage buffer, store the item's outputs themselves and arrive on
+// a second mbarrier; the publisher then frees the buffer for the producers and
+// makes the outputs visible to the other CTAs (release increment of the
+// frame's counter), off the producer's path.
 // Items:
-//  * row item (frame f, band of rows): stage the input rows the band needs in
-//    shared memory as float, resample them with the frame's separable linear-
+//  * row item (frame f, band of rows): stage the uint16 input rows the band
+//    needs in shared memory, resample them with the frame's separable linear-
 //    interpolation taps, multiply by the input chirp (centring phase folded in),
 //    run the Nx-point row DFT in registers (N2-point DFT per thread, twiddle,
 //    exchange through shared memory, N1-point DFTs), multiply by the row's y
