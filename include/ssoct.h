@@ -126,6 +126,8 @@ SSOCT_API ssoct_status ssoct_plan_info(ssoct_plan plan, ssoct_plan_info_t* info)
 /* Device workspace size in bytes (tables, frame ring, L2 scratch ring,
  * sweep-axis intermediate, counters). */
 SSOCT_API ssoct_status ssoct_workspace_size(ssoct_plan plan, size_t* bytes);
+/* The same, under the name of the library's first interface sketch. */
+SSOCT_API ssoct_status ssoct_workspace_bytes(ssoct_plan plan, size_t* bytes);
 
 /* Hand the plan caller-owned device memory of at least ssoct_workspace_size
  * bytes, 256-byte aligned.  Uploads the tables (synchronous copy) on the

@@ -67,6 +67,12 @@ def ssoct_workspace_size(plan):
     return st, n.value
 
 
+def ssoct_workspace_bytes(plan):
+    n = C.c_size_t()
+    st = _abi.lib().ssoct_workspace_bytes(plan, C.byref(n))
+    return st, n.value
+
+
 def ssoct_set_workspace(plan, dev_ptr: int, nbytes: int) -> int:
     return _abi.lib().ssoct_set_workspace(plan, C.c_void_p(dev_ptr), nbytes)
 

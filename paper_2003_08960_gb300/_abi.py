@@ -65,6 +65,7 @@ SIGNATURES = {
                                     C.POINTER(ssoct_plan)]),
     "ssoct_plan_info": (C.c_int, [ssoct_plan, C.POINTER(ssoct_plan_info_t)]),
     "ssoct_workspace_size": (C.c_int, [ssoct_plan, C.POINTER(C.c_size_t)]),
+    "ssoct_workspace_bytes": (C.c_int, [ssoct_plan, C.POINTER(C.c_size_t)]),
     "ssoct_set_workspace": (C.c_int, [ssoct_plan, C.c_void_p, C.c_size_t]),
     "ssoct_push_frames": (C.c_int, [ssoct_plan, C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p]),
     "ssoct_reconstruct_volume": (C.c_int, [ssoct_plan, C.c_void_p, C.c_void_p, C.c_void_p]),

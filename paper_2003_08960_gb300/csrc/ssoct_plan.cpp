@@ -339,6 +339,8 @@ ssoct_status ssoct_workspace_size(ssoct_plan h, size_t* bytes) {
   return SSOCT_OK;
 }
 
+ssoct_status ssoct_workspace_bytes(ssoct_plan h, size_t* bytes) { return ssoct_workspace_size(h, bytes); }
+
 ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
   if (!h) return SSOCT_EINVAL;
   Plan& p = h->p;

@@ -84,6 +84,7 @@ def test_create_plan_validation(ss):
     ss.ssoct_destroy_plan(h)
     st, h = ss.ssoct_create_plan(64, 64, 256, 20e-6, 0.3, lam256)
     st, bytes_plain = ss.ssoct_workspace_size(h)
+    assert ss.ssoct_workspace_bytes(h) == (st, bytes_plain)
     ss.ssoct_destroy_plan(h)
     assert bytes_tc == bytes_plain      # every 256-frame plan keeps the BF16 operand table (the autotuner may switch)
 
