@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(AxStream<NL>::kThreadsAll, 1)
   using S = AxStream<NL>;
   constexpr int N1 = S::N1, N2 = S::N2, T = S::kGroupThreads;
   static_assert(N2 % N1 == 0, "the second stage needs N1 | N2");
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];  // 16 B: the bulk copies need no more
   __shared__ __align__(8) uint64_t full_bar[S::kFull];
   __shared__ unsigned fills[S::kFull];
   const int tid = threadIdx.x;

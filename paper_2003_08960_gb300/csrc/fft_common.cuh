@@ -64,36 +64,10 @@ __device__ __forceinline__ unsigned long long policy_evict_first() {
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-// L2-only (L1 bypassed) complex load / store with an L2 policy.
-__device__ __forceinline__ float2 ld_cg_hint(const float2* a, unsigned long long pol) {
-  float2 v;
-  asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
-               : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol) : "memory");
-  return v;
-}
+// L2-only (L1 bypassed) complex store with an L2 policy.
 __device__ __forceinline__ void st_cg_hint(float2* a, float2 v, unsigned long long pol) {
   asm volatile("st.global.cg.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol)
                : "memory");
-}
-// Read-only 16-byte load, not kept in L1, with an L2 policy.
-__device__ __forceinline__ uint4 ld_nc_hint(const uint4* a, unsigned long long pol) {
-  uint4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
-  return v;
-}
-// Asynchronous prefetch of a contiguous block into L2 (16-byte aligned, size a
-// multiple of 16).
-__device__ __forceinline__ void prefetch_l2_bulk(const void* a, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
-}
-
-// uint16 halves of a 32-bit word to float, exactly: 0x4B000000 | u is 2^23 + u.
-__device__ __forceinline__ float u16lo_to_f(unsigned w) {
-  return __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5410)) - 8388608.0f;
-}
-__device__ __forceinline__ float u16hi_to_f(unsigned w) {
-  return __int_as_float((int)__byte_perm(w, 0x4B00u, 0x5432)) - 8388608.0f;
 }
 
 // Eq. 5 at one pixel of a uint16 frame [.][nx] from its separable taps (weights
