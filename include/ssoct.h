@@ -58,7 +58,7 @@ typedef enum {
   SSOCT_ENOTREADY = 5,    /* fewer than nlambda frames pushed since the gate (re)started */
   SSOCT_EDROPPED = 6,     /* a frame sequence number skipped; the gate restarted */
   SSOCT_ETIMEOUT = 7,     /* a kernel gave up waiting on its own work queue */
-  SSOCT_EUNSUPPORTED = 8  /* valid request outside the sizes this build compiles */
+  SSOCT_EUNSUPPORTED = 8  /* valid request outside the sizes the library is compiled for */
 } ssoct_status;
 
 /* Plan flags. */
@@ -105,7 +105,7 @@ typedef struct {
  *              workspace); such plans do not offer ssoct_reconstruct_sliding
  *              or ssoct_reconstruct_frames_noalloc (EUNSUPPORTED there).
  *   nlambda    frames per sweep = depth bins, N_z of Eq. 3 / the gate of Eq. 7.
- *              This build compiles {16, 32, 64, 96, 128, 160, 200, 256, 512}.
+ *              The library is compiled for {16, 32, 64, 96, 128, 160, 200, 256, 512}.
  *   pitch_m    camera pixel pitch d > 0.
  *   z_m        sensor-to-object distance z != 0 of Eq. 6.
  *   lambda_m   [nlambda] wavelength of each frame of the sweep, > 0; copied.
