@@ -293,11 +293,30 @@ def run_ssoct(args):
     e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
     tc = _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak) if extra and not tc_main else None
     sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if extra else None
+    if sliding is not None and args.size is None:
+        sliding["push_stream"] = _push_stream(args, ss, torch, w, voxels)
     aberration = _aberration(args, ss, torch, synth, stream) if extra else None
     batched = _batched(args, ss, torch, synth, w, frames, stream) if extra else None
 
     # library-free comparison, last so that its buffers do not touch the lines above
     cufft = _cufft_chain(torch, frames, nl, w.ny, w.nx, voxels) if extra and not tc_main else None
+    # error of each form against the FP64 oracle, per volume, outside every timed region
+    parity = None
+    tc_plan = tc.pop("_plan", None) if tc else None
+    if rank == 0 and world == 1 and not args.no_parity:
+        import oracle
+        t_or = time.perf_counter()
+        ref = oracle.reconstruct(w.frames, w.pitch, w.z, w.lambdas, method="fft")
+        t_or = time.perf_counter() - t_or
+        parity = _parity(ss, torch, plan, frames, ref, stream, 1e-3 if tc_main else 1e-5)
+        parity["oracle_s"] = t_or
+        parity["note"] = ("this line's form and schedule vs oracle.reconstruct (float64 scipy.fft) of the same "
+                          "frames, whole volume")
+        if tc_plan is not None:
+            tc["rel_l2_vs_oracle"] = _parity(ss, torch, tc_plan, frames, ref, stream, 1e-3)
+        del ref
+    if tc_plan is not None:
+        del tc_plan
     if args.axial_first:
         # rescale-axial pass: uint16 frames in, half-spectrum planes out; lateral
         # pass: the planes in (each read once from HBM, its conjugate use from L2),
@@ -340,6 +359,7 @@ def run_ssoct(args):
                            "GBps": whole_bytes / (ms * 1e-3) / 1e9,
                            "frac": whole_bytes / (ms * 1e-3) / 1e9 / peak},
         "kernels": kernels,
+        "rel_l2_vs_oracle": parity,
         "e2e": e2e,
         "sliding": sliding,
         "tc_axial": tc,
@@ -370,7 +390,13 @@ def _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world):
     volume and reads it back to pinned host memory (D2H), all inside the timed
     region.  Two plans (two rings) and three streams let step k's H2D overlap
     step k-1's reconstruction and step k-2's D2H, as an acquisition pipeline
-    would run; events keep each ring and volume buffer from being reused early."""
+    would run; events keep each ring and volume buffer from being reused early.
+
+    Right before the pipelined loop the same process times the host link on
+    the same buffers: the H2D copy alone, the D2H copy alone, and both at once
+    on two streams, so the record shows whether the two directions overlap.
+    The loop runs twice, with the D2H as one copy and as four chunks (one
+    cudaMemcpyAsync each), and the line keeps the faster."""
     plans = [plan, ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)]
     vols = [vol, torch.empty_like(vol)]
     host_frames = torch.from_numpy(w.frames.view(np.int16)).pin_memory()
@@ -380,69 +406,96 @@ def _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world):
     ev_comp = [torch.cuda.Event() for _ in range(2)]
     ev_d2h = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = max(3, min(args.steps, 20))
-
-    def e2e_step(k):
-        i = k % 2
-        h = plans[i].handle
-        if k >= 2:
-            s_h2d.wait_event(ev_comp[i])      # the ring's previous gate has been read
-        if ss.ssoct_push_frames(h, host_frames.data_ptr(), nl, False, -1, s_h2d.cuda_stream):
-            raise RuntimeError(ss.ssoct_last_error(h))
-        ev_h2d[i].record(s_h2d)
-        s_comp.wait_event(ev_h2d[i])
-        if k >= 2:
-            s_comp.wait_event(ev_d2h[i])      # the volume buffer has been read back
-        if ss.ssoct_reconstruct_volume(h, vols[i].data_ptr(), 0, s_comp.cuda_stream):
-            raise RuntimeError(ss.ssoct_last_error(h))
-        ev_comp[i].record(s_comp)
-        s_d2h.wait_event(ev_comp[i])
-        with torch.cuda.stream(s_d2h):
-            host_vols[i].copy_(vols[i], non_blocking=True)
-        ev_d2h[i].record(s_d2h)
-
-    for k in range(2):
-        e2e_step(k)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    h2d_bytes = int(host_frames.numel() * 2)
+    d2h_bytes = int(host_vols[0].numel() * 4)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s_h2d)
-    for k in range(2, 2 + e2e_steps):
-        e2e_step(k)
-    s_d2h.wait_stream(s_h2d)
-    s_d2h.wait_stream(s_comp)
-    e1.record(s_d2h)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    for pl in plans:
-        if ss.ssoct_sync(pl.handle, 0):
-            raise RuntimeError("kernel error: " + ss.ssoct_last_error(pl.handle))
-    # the link's floor for the same bytes: the same H2D and D2H copies, with no
-    # kernels, on the same two streams
     dev_frames = torch.empty(host_frames.shape, dtype=host_frames.dtype, device="cuda")
 
-    def copy_step(i):
-        with torch.cuda.stream(s_h2d):
-            dev_frames.copy_(host_frames, non_blocking=True)
-        with torch.cuda.stream(s_d2h):
-            host_vols[i].copy_(vols[i], non_blocking=True)
+    def link(h2d: bool, d2h: bool, reps: int = 5):
+        """ms per repetition of the H2D and/or D2H copy (both: concurrently on two streams)."""
+        def once(i):
+            if h2d:
+                with torch.cuda.stream(s_h2d):
+                    dev_frames.copy_(host_frames, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s_d2h):
+                    host_vols[i % 2].copy_(vols[i % 2], non_blocking=True)
+        once(0)
+        torch.cuda.synchronize()
+        e0.record(s_h2d)
+        s_d2h.wait_event(e0)
+        for i in range(reps):
+            once(i)
+        s_h2d.wait_stream(s_d2h)
+        e1.record(s_h2d)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
 
-    for k in range(2):
-        copy_step(k % 2)
-    torch.cuda.synchronize()
-    e0.record(s_h2d)
-    s_d2h.wait_event(e0)
-    for k in range(e2e_steps):
-        copy_step(k % 2)
-    s_h2d.wait_stream(s_d2h)
-    e1.record(s_h2d)
-    torch.cuda.synchronize()
-    copy_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d_ms, d2h_ms, both_ms = link(True, False), link(False, True), link(True, True)
+    link_rec = {"h2d_ms": h2d_ms, "h2d_GBps": h2d_bytes / (h2d_ms * 1e-3) / 1e9,
+                "d2h_ms": d2h_ms, "d2h_GBps": d2h_bytes / (d2h_ms * 1e-3) / 1e9,
+                "both_ms": both_ms, "both_GBps": (h2d_bytes + d2h_bytes) / (both_ms * 1e-3) / 1e9,
+                "overlap": (h2d_ms + d2h_ms) / both_ms,
+                "note": "pinned host <-> device copies of one step's frames and volume, timed in this "
+                        "process right before the pipelined loop; overlap = (H2D alone + D2H alone) / "
+                        "both at once (1 = serialised, 2 = fully overlapped)"}
+
+    def run_loop(chunks: int) -> float:
+        flat = [v.view(-1) for v in vols]
+        hflat = [v.view(-1) for v in host_vols]
+        n = flat[0].numel()
+        bounds = [n * c // chunks for c in range(chunks + 1)]
+
+        def e2e_step(k):
+            i = k % 2
+            h = plans[i].handle
+            if k >= 2:
+                s_h2d.wait_event(ev_comp[i])      # the ring's previous gate has been read
+            if ss.ssoct_push_frames(h, host_frames.data_ptr(), nl, False, -1, s_h2d.cuda_stream):
+                raise RuntimeError(ss.ssoct_last_error(h))
+            ev_h2d[i].record(s_h2d)
+            s_comp.wait_event(ev_h2d[i])
+            if k >= 2:
+                s_comp.wait_event(ev_d2h[i])      # the volume buffer has been read back
+            if ss.ssoct_reconstruct_volume(h, vols[i].data_ptr(), 0, s_comp.cuda_stream):
+                raise RuntimeError(ss.ssoct_last_error(h))
+            ev_comp[i].record(s_comp)
+            s_d2h.wait_event(ev_comp[i])
+            with torch.cuda.stream(s_d2h):
+                for c in range(chunks):
+                    hflat[i][bounds[c]:bounds[c + 1]].copy_(flat[i][bounds[c]:bounds[c + 1]], non_blocking=True)
+            ev_d2h[i].record(s_d2h)
+
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0.record(s_h2d)
+        for k in range(2, 2 + e2e_steps):
+            e2e_step(k)
+        s_d2h.wait_stream(s_h2d)
+        s_d2h.wait_stream(s_comp)
+        e1.record(s_d2h)
+        torch.cuda.synchronize()
+        for pl in plans:
+            if ss.ssoct_sync(pl.handle, 0):
+                raise RuntimeError("kernel error: " + ss.ssoct_last_error(pl.handle))
+        return e0.elapsed_time(e1) / e2e_steps
+
+    by_chunks = {1: run_loop(1), 4: run_loop(4)}
+    chunks = min(by_chunks, key=by_chunks.get)
+    e2e_ms = by_chunks[chunks]
+    # the link's floor for the same bytes, right after the loop: the same H2D and
+    # D2H copies, with no kernels, on the same two streams
+    copy_ms = link(True, True, reps=e2e_steps)
     e2e_ms, e2e_value = aggregate(e2e_ms, voxels, world, dist if world > 1 else None, device="cuda")
-    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_frames.numel() * 2),
-            "d2h_bytes_per_step": int(host_vols[0].numel() * 4), "ms_per_step": e2e_ms,
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+            "d2h_bytes_per_step": d2h_bytes, "ms_per_step": e2e_ms,
+            "ms_by_d2h_chunks": by_chunks, "d2h_chunks": chunks,
             "copy_floor_ms": copy_ms, "frac_of_copy_floor": copy_ms / e2e_ms,
+            "link_before_loop": link_rec,
             "pipeline": "2 rings, H2D / reconstruct / D2H on 3 streams; copy floor = the same copies "
                         "alone on the same streams (pinned host memory, host link bound)"}
 
@@ -519,10 +572,70 @@ def _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream, step_frames
             "paper": "38 volumes/s (TITAN Xp, sliding 256-frame gate, 512 frames/s)"}
 
 
+def _push_stream(args, ss, torch, w, voxels, step_frames=13, fps=512.0):
+    """The paper's acquisition pattern (Table 1: 512 frames/s, about 38 volumes/s
+    from a sliding 256-frame gate): frames arrive one at a time in pinned host
+    memory, each is pushed on its own (ssoct_push_frames, one 2 MiB H2D copy),
+    and after every `step_frames` frames the gate of the last nlambda frames is
+    reconstructed (ssoct_reconstruct_sliding).  Run twice: paced by the host at
+    `fps` frames per second, and as fast as the host can issue.  Latency is
+    GPU time from the start of the gate's last frame copy to the end of its
+    volume (CUDA events on the stream)."""
+    import time
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)
+    h = plan.handle
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    host = torch.from_numpy(w.frames.view(np.int16)).pin_memory()
+    fbytes = host[0].numel() * 2
+    vol, _ = plan.empty_volume()
+    nl = w.nlambda
+
+    def run(n_frames, paced, seq0):
+        marks = []
+        t_start = time.perf_counter()
+        for i in range(n_frames):
+            if paced:
+                due = t_start + i / fps
+                while time.perf_counter() < due:
+                    pass
+            last = (i + 1) % step_frames == 0 and seq0 + i + 1 >= nl   # a full gate is in
+            if last:
+                a = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            if ss.ssoct_push_frames(h, host.data_ptr() + ((seq0 + i) % nl) * fbytes, 1, False, seq0 + i, sp):
+                raise RuntimeError(ss.ssoct_last_error(h))
+            if last:
+                if ss.ssoct_reconstruct_sliding(h, vol.data_ptr(), 0, sp):
+                    raise RuntimeError(ss.ssoct_last_error(h))
+                b = torch.cuda.Event(enable_timing=True)
+                b.record(stream)
+                marks.append((a, b))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_start
+        if ss.ssoct_sync(h, sp):
+            raise RuntimeError("kernel error: " + ss.ssoct_last_error(h))
+        lat = sorted(a.elapsed_time(b) for a, b in marks) or [float("nan")]
+        return {"frames": n_frames, "wall_s": wall, "frames_per_s": n_frames / wall,
+                "volumes_per_s": len(marks) / wall, "Gvoxel_per_s": len(marks) * voxels / wall / 1e9,
+                "latency_ms": {"median": statistics.median(lat), "max": lat[-1]}}
+
+    # fill the gate, then warm up
+    run(nl + 2 * step_frames, False, 0)
+    seq = nl + 2 * step_frames
+    fast = run(2 * nl, False, seq)
+    seq += 2 * nl
+    paced = run(nl, True, seq)
+    return {"step_frames": step_frames, "fast": fast, "paced_512fps": paced,
+            "form": "one ssoct_push_frames per frame from pinned host memory (2 MiB H2D each), "
+                    "ssoct_reconstruct_sliding after every step_frames frames; latency = GPU time from the "
+                    "start of the gate's last frame copy to the end of its volume",
+            "paper": "512 frames/s in, up to 38 volumes/s out (TITAN Xp)"}
+
+
 def _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak):
     """The same step with the axial DFT on the tensor cores (SSOCT_FLAG_TC_AXIAL),
-    on the same frames; vol holds the FP32 form's volume of those frames, and the
-    relative L2 distance between the two volumes is reported beside the rate."""
+    on the same frames; its error against the FP64 oracle is added by the caller."""
     if w.nlambda != 256:
         return None
     plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=ss.SSOCT_FLAG_TC_AXIAL)
@@ -552,7 +665,6 @@ def _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak):
     _, lat_ms, ax_ms, calls = ss.ssoct_profile_read(h)
     ax_ms /= max(calls, 1)
     ax_bytes = voxels * (8 + 4)
-    d = (vt.double() - vol.double()).norm() / vol.double().norm()
     # tensor work: per 32-pixel tile, 4 blocks x 3 products (hi.hi, hi.lo,
     # lo.hi) x 2 stages of a 128 x 32 x 32 real GEMM = 768 flop per voxel
     tflops = TC_FLOP_PER_VOXEL * voxels / (ax_ms * 1e-3) / 1e12
@@ -563,8 +675,30 @@ def _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak):
             "tensor_roofline": {"bound": "tensor", "achieved": tflops, "peak": tpeak, "peak_kind": tkind,
                                 "unit": "TFLOP/s", "frac": tflops / tpeak,
                                 "flop_per_voxel": TC_FLOP_PER_VOXEL},
-            "rel_l2_vs_fp32_volume": float(d),
-            "form": "axial DFT as two 16-point tcgen05 MMA stages, bf16 hi+lo operands, fp32 accumulate in TMEM"}
+            "form": "axial DFT as two 16-point tcgen05 MMA stages, bf16 hi+lo operands, fp32 accumulate in TMEM",
+            "_plan": plan}
+
+
+def _parity(ss, torch, plan, frames, ref, stream, bound):
+    """Relative L2 distance of one reconstruction from the FP64 oracle's volume
+    ref [nl][ny][nx] (complex128): on the complex V and on |V|^2, summed over
+    chunks of depth bins in float64."""
+    vol, cplx = plan.reconstruct(frames, complex_out=True, stream=stream)
+    torch.cuda.synchronize()
+    if ss.ssoct_sync(plan.handle, stream.cuda_stream):
+        raise RuntimeError("kernel error: " + ss.ssoct_last_error(plan.handle))
+    v = cplx.cpu().numpy()
+    p = vol.cpu().numpy()
+    del vol, cplx
+    acc = np.zeros(4)
+    for q0 in range(0, v.shape[0], 16):
+        r = ref[q0:q0 + 16]
+        d = v[q0:q0 + 16].astype(np.complex128) - r
+        rp = r.real ** 2 + r.imag ** 2
+        dp = p[q0:q0 + 16].astype(np.float64) - rp
+        acc += [(d.real ** 2 + d.imag ** 2).sum(), rp.sum(), (dp ** 2).sum(), (rp ** 2).sum()]
+    return {"complex": float(np.sqrt(acc[0] / acc[1])), "intensity": float(np.sqrt(acc[2] / acc[3])),
+            "bound_complex": bound}
 
 
 def _cufft_chain(torch, frames, nl, ny, nx, voxels, steps=10):
@@ -734,6 +868,7 @@ def main():
     ap.add_argument("--impl", default="ssoct", choices=["ssoct", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true", help="skip the per-volume comparison with the FP64 oracle")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default schedule")
     ap.add_argument("--axial-first", action="store_true",
                     help="Eq. 5 + Eq. 7 before Eq. 6 (SSOCT_FLAG_AXIAL_FIRST) for the main line")

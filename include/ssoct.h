@@ -176,11 +176,16 @@ SSOCT_API ssoct_status ssoct_reconstruct_frames(ssoct_plan plan, const uint16_t*
  * allocating library routine).  Plans whose workspace would exceed 64 MiB get
  * SSOCT_EUNSUPPORTED with a message saying so (e.g. 256 x 256 x 64 fits,
  * 512 x 512 x 32 does not).  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the array and rewrites the tables and zeroes the
- * counters itself; calls whose work overlaps on the GPU (other streams or host
- * threads) race on it, so serialise them.  A kernel time-out on this path is not
- * reported by ssoct_sync. */
+ * device address (cudaGetSymbolAddress) and SM count; make that first call
+ * before any stream capture.  Host threads may make their first calls at once
+ * (the look-up is done once per device, under a lock).  The address is kept for
+ * the life of the process, so after a device reset (cudaDeviceReset) this entry
+ * point needs a new process.  Every call shares the array and rewrites the
+ * tables and zeroes the counters itself; calls whose work overlaps on the GPU
+ * (other streams or host threads) race on it, so serialise them.  A kernel
+ * time-out of this call is reported by ssoct_sync on the same plan (SSOCT_ETIMEOUT),
+ * provided no other no-allocation call on that device comes in between: the
+ * error word lives in the shared array. */
 SSOCT_API ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan plan, const uint16_t* frames_dev,
                                                         float* vol_dev, void* complex_dev, void* stream);
 
@@ -249,7 +254,8 @@ SSOCT_API ssoct_status ssoct_get_cuts(ssoct_plan plan, const float* vol_dev, int
 
 /* Wait for `stream` and report what the kernels recorded: ETIMEOUT if a kernel
  * gave up waiting on its work queue (its output is then incomplete), ECUDA on a
- * CUDA error, else OK.  Clears the recorded error. */
+ * CUDA error, else OK.  Clears the recorded error.  After a
+ * ssoct_reconstruct_frames_noalloc call it reports that call's kernels too. */
 SSOCT_API ssoct_status ssoct_sync(ssoct_plan plan, void* stream);
 
 /* Stage timing.  enable != 0: every reconstruct call from now on records CUDA

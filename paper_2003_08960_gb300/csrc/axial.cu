@@ -525,11 +525,15 @@ bool axial_supported(int nl) {
   return false;
 }
 
-cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s) {
-#define X(a) if (p.nl == a) return launch<a>(ap, p.num_sms, s);
+cudaError_t launch_axial_with(const Plan& p, const AxialParams& ap, int num_sms, cudaStream_t s) {
+#define X(a) if (p.nl == a) return launch<a>(ap, num_sms, s);
   SSOCT_AXIAL_SIZES(X)
 #undef X
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_axial(const Plan& p, const AxialParams& ap, cudaStream_t s) {
+  return launch_axial_with(p, ap, p.num_sms, s);
 }
 
 // The three orthogonal cuts: plain gathers from the volume [q][y][x].

@@ -288,7 +288,9 @@ def codelet(n, sign):
 
 def main(out_path):
     parts = [
-        "// Generated by gen_codelets.py: straight-line in-register DFTs.  Do not edit.\n",
+        "// Generated by gen_codelets.py: straight-line in-register DFTs.  Do not edit.\n"
+        "// The build rewrites this file; the copy kept in the tree must equal the\n"
+        "// generator's output (checked by tests/test_codelets_host.py).\n",
         "#pragma once\n#include <cuda_runtime.h>\n\nnamespace ssoct {\n",
         "template <int N, int SIGN> struct Dft;\n",
         "template <int SIGN> struct Dft<1, SIGN> {\n  template <int ST, int OFF>\n"

@@ -17,7 +17,13 @@
 // the last call's contents: each call rewrites the tables and zeroes the
 // counters before its kernels run, and calls that overlap on the GPU (different
 // streams, or different host threads) race on it.
+//
+// A kernel that gives up a bounded wait leaves its error word in the array;
+// ssoct_sync on the same plan reads it (noalloc_error_word) and reports
+// SSOCT_ETIMEOUT, as it does for the workspace path.
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "ssoct_internal.h"
 
@@ -29,9 +35,36 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of g_noalloc_scratch and SM count, per device (set on first use).
-char* g_scratch_addr[kMaxDevices] = {};
-int g_num_sms[kMaxDevices] = {};
+// Device address of g_noalloc_scratch and SM count, per device, set once by the
+// first call on that device.  Host threads may make their first calls at the
+// same time: the set-up runs under a mutex and publishes the address last
+// (release), so a thread that sees the address also sees the SM count.
+std::atomic<char*> g_scratch_addr[kMaxDevices] = {};
+std::atomic<int> g_num_sms[kMaxDevices] = {};
+std::mutex g_setup_mutex;
+
+// The array's device address on device dev (the current one), looked up once.
+cudaError_t scratch_on_device(int dev, char** addr, int* sms) {
+  char* a = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    a = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!a) {
+      // In host code the name g_noalloc_scratch is only a host-side stand-in,
+      // so the kernels get this address instead.
+      cudaError_t e = cudaGetSymbolAddress((void**)&a, g_noalloc_scratch);
+      if (e != cudaSuccess) return e;
+      int n = 0;
+      e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      g_num_sms[dev].store(n, std::memory_order_relaxed);
+      g_scratch_addr[dev].store(a, std::memory_order_release);
+    }
+  }
+  *addr = a;
+  *sms = g_num_sms[dev].load(std::memory_order_relaxed);
+  return cudaSuccess;
+}
 
 ssoct_status fail(Plan& p, ssoct_status s, const std::string& msg) {
   p.last_error = msg;
@@ -64,19 +97,10 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(p, SSOCT_EUNSUPPORTED, "device index beyond the no-allocation table");
   // One-time set-up on this device (the current one): the array's device address.
-  // In host code the name g_noalloc_scratch is only a host-side stand-in, so the
-  // kernels get this address instead.
-  if (!g_scratch_addr[dev]) {
-    char* addr = nullptr;
-    e = cudaGetSymbolAddress((void**)&addr, g_noalloc_scratch);
-    if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
-    g_num_sms[dev] = sms;
-    g_scratch_addr[dev] = addr;
-  }
-  char* ws = g_scratch_addr[dev];
+  char* ws = nullptr;
+  int num_sms = 0;
+  e = scratch_on_device(dev, &ws, &num_sms);
+  if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("no-allocation set-up: ") + cudaGetErrorString(e));
   cudaStream_t s = (cudaStream_t)stream;
 
   // Tables of this plan (the previous call may have left another plan's), then
@@ -104,6 +128,14 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   }
   e = cudaMemsetAsync(ws + p.off_ctr, 0, sizeof(Counters) + 2 * sizeof(unsigned) * (size_t)p.nl, s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("counter reset: ") + cudaGetErrorString(e));
+  if (p.inject_skip) {
+    // start the ticket counter past the first items (ssoct_inject_stall); the
+    // copy reads the plan's own field, and the sync keeps it a test-only cost
+    e = cudaMemcpyAsync(ws + p.off_ctr, &p.inject_skip, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("stall injection: ") + cudaGetErrorString(e));
+  }
+  p.noalloc_device = dev;
 
   alignas(64) unsigned char tmap[128];
   if (!encode_scratch_map_at(p, ws + p.off_scratch, tmap))
@@ -131,7 +163,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   lp.stage_rows = p.stage_rows;
   lp.stage_bytes = 0;
   lp.wait_ns = p.wait_ns;
-  e = launch_lateral_with(p, lp, tmap, g_num_sms[dev], s);
+  e = launch_lateral_with(p, lp, tmap, num_sms, s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("lateral kernel launch: ") + cudaGetErrorString(e));
 
   AxialParams ap;
@@ -146,7 +178,25 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
   ap.err = &lp.ctr->err;
   e = p.use_tc ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb), &lp.ctr->err, s)
-                                      : launch_axial(p, ap, s);
+                                      : launch_axial_with(p, ap, num_sms, s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("axial kernel launch: ") + cudaGetErrorString(e));
   return SSOCT_OK;
 }
+
+namespace ssoct {
+
+cudaError_t noalloc_error_word(Plan& p, unsigned* err) {
+  *err = 0u;
+  const int dev = p.noalloc_device;
+  if (dev < 0) return cudaSuccess;
+  char* ws = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!ws) return cudaSuccess;
+  Counters c;
+  cudaError_t e = cudaMemcpy(&c, ws + p.off_ctr, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  *err = c.err;
+  p.noalloc_device = -1;
+  return cudaSuccess;
+}
+
+}  // namespace ssoct

@@ -196,6 +196,7 @@ struct Plan {
   size_t off_aplanes = 0;
   char* ws = nullptr;
   int device = -1;
+  int noalloc_device = -1;   // device of the plan's last no-allocation call (-1: none)
   int num_sms = 0;
   alignas(64) unsigned char tmap[128];        // CUtensorMap of the scratch ring (column bands)
   // frame ring state
@@ -273,6 +274,12 @@ Plan& plan_of(ssoct_plan h);
 bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out);
 cudaError_t launch_lateral_with(const Plan& p, const LateralParams& lp, const void* tmap,
                                 int num_sms, cudaStream_t s);
+// The axial launch with the SM count given explicitly (the persistent streaming
+// form sizes its grid by it); launch_axial passes the plan's own.
+cudaError_t launch_axial_with(const Plan& p, const AxialParams& ap, int num_sms, cudaStream_t s);
+// Error word of the last no-allocation call made with this plan (0 if none, or
+// if that call's kernels met no time-out); read after the caller's stream sync.
+cudaError_t noalloc_error_word(Plan& p, unsigned* err);
 // Whole-frame window: the lateral kernel then needs no window bounds checks.
 inline bool lateral_full_window(const Plan& p) { return p.x0 == 0 && p.y0 == 0 && p.wx == p.nx && p.wy == p.ny; }
 

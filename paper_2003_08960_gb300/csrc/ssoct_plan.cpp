@@ -694,6 +694,14 @@ ssoct_status ssoct_sync(ssoct_plan h, void* stream) {
   Plan& p = h->p;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(&p, e, "stream synchronize");
+  // the last no-allocation call's kernels leave their error word in that
+  // path's device array, not in the workspace
+  unsigned noalloc_err = 0u;
+  e = noalloc_error_word(p, &noalloc_err);
+  if (e != cudaSuccess) return cuda_fail(&p, e, "error word read (no-allocation path)");
+  if (noalloc_err & kErrTimeout) return fail(&p, SSOCT_ETIMEOUT, "lateral kernel gave up waiting on its work queue (no-allocation call)");
+  if (noalloc_err & kErrAxial) return fail(&p, SSOCT_ETIMEOUT, "axial kernel gave up waiting on its stage buffers (no-allocation call)");
+  if (noalloc_err) return fail(&p, SSOCT_ETIMEOUT, "tensor-core axial kernel gave up waiting on its MMAs (no-allocation call)");
   if (!p.ws) return SSOCT_OK;
   Counters c;
   e = cudaMemcpy(&c, p.ws + p.off_ctr, sizeof(c), cudaMemcpyDeviceToHost);

@@ -192,6 +192,22 @@ def pin_axial_parseval(o):
     assert np.allclose(np.sum(np.abs(v) ** 2, axis=0), 64 * np.sum(np.abs(h) ** 2, axis=0), rtol=1e-12)
 
 
+def pin_intensity(o):
+    """The envelope of the cut formulas after Eq. 7 is |V|^2 = Re^2 + Im^2:
+    hand values, then Parseval through the axial transform (sum_q |V_q|^2 =
+    N sum_t |H_t|^2, the right side summed here from squared real and imaginary
+    parts), and the three cuts are plain slices of it."""
+    v = np.array([3 + 4j, -1j, 0.5 - 0.5j, -2 + 0j, 0j])
+    assert np.array_equal(o.intensity(v), np.array([25.0, 1.0, 0.5, 4.0, 0.0]))
+    rng = np.random.default_rng(23)
+    h = rng.normal(size=(16, 4, 5)) + 1j * rng.normal(size=(16, 4, 5))
+    p = o.intensity(o.axial(h, method="fft"))
+    assert p.shape == h.shape and np.isrealobj(p) and (p >= 0).all()
+    assert np.isclose(p.sum(), 16 * (h.real ** 2 + h.imag ** 2).sum(), rtol=1e-12)
+    xy, xz, yz = o.cuts(p, 3, 1, 7)
+    assert np.array_equal(xy, p[7]) and np.array_equal(xz, p[:, 1, :]) and np.array_equal(yz, p[:, :, 3])
+
+
 # ---------------------------------------------------------------- end to end
 
 def point_case(n=64, nl=32, X_px=3.3, Y_px=-5.2, delta=0.1e-3, ny=None):
@@ -266,6 +282,6 @@ def pin_pixel_sample(o):
 ALL_PINS = [
     pin_rescale_identity, pin_rescale_affine, pin_rescale_hand_values, pin_rescale_zero_outside,
     pin_fresnel_convolution, pin_fresnel_matched_chirp, pin_fresnel_parseval,
-    pin_axial_loops, pin_axial_dirichlet, pin_axial_parseval,
+    pin_axial_loops, pin_axial_dirichlet, pin_axial_parseval, pin_intensity,
     pin_point_scatterer, pin_chromatic_compensation, pin_pixel_sample,
 ]

@@ -72,3 +72,14 @@ def test_codelets_match_dft(codelet_output):
         assert np.array_equal(got[0::2], x[0::2])
         seen += 1
     assert seen == 2 * len(gen_codelets.SIZES)
+
+
+def test_committed_codelets_match_the_generator(tmp_path):
+    """fft_codelets.cuh is written by gen_codelets.py at every build and also
+    kept in the tree so the sources read on their own; the committed copy must
+    be exactly what the generator writes."""
+    out = tmp_path / "fft_codelets.cuh"
+    gen_codelets.main(str(out))
+    with open(os.path.join(CSRC, "fft_codelets.cuh")) as f:
+        committed = f.read()
+    assert out.read_text() == committed, "fft_codelets.cuh differs from gen_codelets.py's output: rerun the build"

@@ -97,3 +97,49 @@ def test_autograd_backward_and_descent(ss):
         loss.backward()
         opt.step()
     assert float(sharpness(plan, f, c.detach(), z.detach())) < first
+
+
+def test_config5_gradient_against_finite_differences_of_the_gpu_loss(ss):
+    """Central differences of the GPU's own loss (not the oracle's) at the
+    512x512x128 speckle workload, 15 coefficients ~ N(0, 0.5 rad), z + 5 mm,
+    with the steps h = 1e-3 rad for c_j and 1e-3 mm for z.
+
+    Noise floor of the difference quotient: the loss is reduced in FP64 from the
+    FP32 volume with atomics, so two evaluations at the same point differ by
+    rounding only; that spread (measured here) divided by h bounds the quotient's
+    noise, and the truncation error of a central difference is O(h^2).  Each
+    sampled component must agree with the adjoint gradient to 1e-3 of the
+    gradient's norm, far above both."""
+    w = synth.workload("mid_512x512x128")
+    coeffs = np.random.default_rng(5).normal(0.0, 0.5, 15)
+    z = 0.305
+    plan = ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, 0.3, w.lambdas, flags=ss.SSOCT_FLAG_PUPIL)
+    f = _dev(w.frames)
+    vol = plan.empty_volume()[0]
+
+    def loss(c, zz):
+        l, _, _ = plan.sharpness(f, c, zz, out=vol)
+        return l
+
+    l0, g, _ = plan.sharpness(f, coeffs, z, out=vol)
+    noise = max(abs(loss(coeffs, z) - l0) for _ in range(3))
+    gnorm = float(np.linalg.norm(g))
+    h_c, h_z = 1e-3, 1e-6
+    checks = [("z", 0, None)] + [(f"c_{j}", j, j - 1) for j in (1, 2, 4, 7, 11, 15)]
+    worst = 0.0
+    for name, gi, ci in checks:
+        if ci is None:
+            fd = (loss(coeffs, z + h_z) - loss(coeffs, z - h_z)) / (2 * h_z)
+            scale = gnorm
+        else:
+            cp, cm = coeffs.copy(), coeffs.copy()
+            cp[ci] += h_c
+            cm[ci] -= h_c
+            fd = (loss(cp, z) - loss(cm, z)) / (2 * h_c)
+            scale = float(np.linalg.norm(g[1:]))
+        err = abs(fd - g[gi]) / scale
+        worst = max(worst, err)
+        print(f"{name}: adjoint {g[gi]:+.6e}  central difference {fd:+.6e}  |diff|/|g| {err:.1e}")
+        assert err <= 1e-3, (name, fd, g[gi])
+    print(f"loss {l0:.6e}; repeat-evaluation spread {noise:.1e} (quotient noise <= {noise / h_c:.1e} per rad, "
+          f"{noise / h_z:.1e} per m); worst |diff|/|g| {worst:.1e}")

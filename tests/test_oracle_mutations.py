@@ -40,6 +40,10 @@ MUTATIONS = {
     "rescale_skipped": ("ip = rescale(frames[t], s[t])", "ip = np.asarray(frames[t], dtype=np.float64)"),
     "lambda_t_in_fresnel": ("h[t - t0] = fresnel(ip, pitch, z, lam1,", "h[t - t0] = fresnel(ip, pitch, z, lambdas[t],"),
     "reconstructed_pixel_wrong_n": ("return lam * z / (n * pitch)", "return lam * z / pitch"),
+    "intensity_imag_dropped": ("return v.real ** 2 + v.imag ** 2", "return v.real ** 2"),
+    "intensity_magnitude_not_squared": ("return v.real ** 2 + v.imag ** 2", "return np.sqrt(v.real ** 2 + v.imag ** 2)"),
+    "intensity_complex_square": ("return v.real ** 2 + v.imag ** 2", "return (v * v).real"),
+    "cuts_xz_yz_swapped": ("p[:, y0, :].copy(), p[:, :, x0].copy()", "p[:, :, x0].copy(), p[:, y0, :].copy()"),
 }
 
 
