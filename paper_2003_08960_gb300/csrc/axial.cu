@@ -127,6 +127,31 @@ __device__ __forceinline__ void axial_fill(const AxialParams& p, unsigned char* 
               &full_bar[f]);
 }
 
+// End of a streaming tile: the depth bins q = k2 + N2 k1 this thread holds (a[])
+// for window pixel (kxw, kyw): |V|^2 |K|^2 (|V| |K| if MAG) into the volume and,
+// if CPLX, V with the output chirp and K into the complex volume.
+template <int NL, bool MAG, bool CPLX>
+__device__ __forceinline__ void axial_epilogue(const AxialParams& p, const float2* a, int j1, int kyw, int kxw) {
+  constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  const size_t plane = (size_t)p.wy * p.wx;
+  float* vol = p.vol + (size_t)kyw * p.wx + kxw;
+  float2 of = make_float2(0.f, 0.f);
+  if constexpr (CPLX) of = cmul(ldg2(p.ox + kxw), ldg2(p.oy + kyw));
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int ii = decltype(I)::value;
+    const int k2 = j1 + N1 * ii;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const int q = k2 + N2 * k1;
+      const float2 v = a[ii * N1 + k1];
+      float pw = fmaf(v.x, v.x, v.y * v.y) * p.power_scale;
+      if constexpr (MAG) pw = sqrtf(pw);
+      __stcs(vol + (size_t)q * plane, pw);
+      if constexpr (CPLX) __stcs(p.cplx + (size_t)q * plane + (size_t)kyw * p.wx + kxw, cmul(v, of));
+    }
+  });
+}
+
 template <int NL>
 __global__ void __launch_bounds__(AxStream<NL>::kThreadsAll, 1)
     axial_stream_kernel(const __grid_constant__ AxialParams p) {
@@ -153,7 +178,6 @@ __global__ void __launch_bounds__(AxStream<NL>::kThreadsAll, 1)
   const int lt = tid % T;
   const int pix = lt % kTile;
   const int j1 = lt / kTile;
-  const size_t plane = (size_t)p.wy * p.wx;
   for (int i = g, prev = -1;; prev = i, i += kAxGroups) {
     group_sync<T>(1 + g);  // every thread of the group is done with tile prev's buffer
     if (lt == 0 && prev >= 0 && prev + S::kStages < mine) axial_fill<NL>(p, smem, full_bar, fills, prev + S::kStages);
@@ -185,22 +209,15 @@ __global__ void __launch_bounds__(AxStream<NL>::kThreadsAll, 1)
     const int kyw = gt / p.ntx;
     const int kxw = (gt - kyw * p.ntx) * kTile + pix;
     if (kxw >= p.wx) continue;
-    float* vol = p.vol + (size_t)kyw * p.wx + kxw;
-    float2 of = make_float2(0.f, 0.f);
-    if (p.cplx) of = cmul(ldg2(p.ox + kxw), ldg2(p.oy + kyw));
-    static_for<0, N2 / N1>([&](auto I) {
-      constexpr int ii = decltype(I)::value;
-      const int k2 = j1 + N1 * ii;
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const int q = k2 + N2 * k1;
-        const float2 v = a[ii * N1 + k1];
-        float pw = fmaf(v.x, v.x, v.y * v.y) * p.power_scale;
-        if (p.magnitude) pw = sqrtf(pw);
-        __stcs(vol + (size_t)q * plane, pw);
-        if (p.cplx) __stcs(p.cplx + (size_t)q * plane + (size_t)kyw * p.wx + kxw, cmul(v, of));
-      }
-    });
+    // the options are tested once per tile: inside the unrolled loop they were
+    // predicated on every value
+    if (p.cplx) {
+      if (p.magnitude) axial_epilogue<NL, true, true>(p, a, j1, kyw, kxw);
+      else axial_epilogue<NL, false, true>(p, a, j1, kyw, kxw);
+    } else {
+      if (p.magnitude) axial_epilogue<NL, true, false>(p, a, j1, kyw, kxw);
+      else axial_epilogue<NL, false, false>(p, a, j1, kyw, kxw);
+    }
   }
   // copies still in flight (after a time-out) write this CTA's shared memory:
   // they land before it exits.  The last fill of each barrier is its latest

@@ -147,13 +147,20 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   float2 cyv;
   if constexpr (AF) {
     const float2* in2 = reinterpret_cast<const float2*>(buf) + r * NX;
-    const bool cj = af_bin(f, p.nl) > p.nl / 2;
+    // bins above N/2 use the conjugate plane: conj(v) c = (v.x c.x + v.y c.y, v.x c.y - v.y c.x)
+    if (af_bin(f, p.nl) > p.nl / 2) {
 #pragma unroll
-    for (int j2 = 0; j2 < N2; ++j2) {
-      const int n = j1 + N1 * j2;
-      float2 v = in2[n];
-      if (cj) v.y = -v.y;
-      a[j2] = cmul(v, cxs[n]);
+      for (int j2 = 0; j2 < N2; ++j2) {
+        const int n = j1 + N1 * j2;
+        const float2 v = in2[n], c = cxs[n];
+        a[j2] = make_float2(fmaf(v.x, c.x, v.y * c.y), fmaf(v.x, c.y, -v.y * c.x));
+      }
+    } else {
+#pragma unroll
+      for (int j2 = 0; j2 < N2; ++j2) {
+        const int n = j1 + N1 * j2;
+        a[j2] = cmul(in2[n], cxs[n]);
+      }
     }
     cyv = ldg2(p.cy + y);
   } else {
@@ -220,6 +227,36 @@ __device__ __forceinline__ int col_row(int j1, int k2) {
   else return j1 + N1 * k2;
 }
 
+// Axial-first order, end of a column item: V of depth bin q at window column
+// kxw for the rows this thread holds (a[], rows k2 + N2 k1 of the column DFT):
+// |V|^2 |K|^2 (|V| |K| if MAG) into the volume and, if CPLX, V with the output
+// chirp and K into the complex volume.
+template <int NY, bool FW, bool MAG, bool CPLX>
+__device__ __forceinline__ void af_epilogue(const LateralParams& p, const Desc& d, const float2* a, int j1,
+                                            int kxw) {
+  constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
+  const int q = af_bin(d.f, p.nl);
+  float* vdst = p.vol + (size_t)q * p.wy * p.wx + kxw;
+  float2 ox = make_float2(0.f, 0.f);
+  if constexpr (CPLX) ox = ldg2(p.ox + kxw);
+  static_for<0, N2 / N1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int k2 = j1 + N1 * i;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const int kyw = k2 + N2 * k1 - (FW ? 0 : p.y0);
+      if (FW || (kyw >= 0 && kyw < p.wy)) {
+        const float2 v = a[i * N1 + k1];
+        float pw = fmaf(v.x, v.x, v.y * v.y) * p.power_scale;
+        if constexpr (MAG) pw = sqrtf(pw);
+        __stcs(vdst + (size_t)kyw * p.wx, pw);
+        if constexpr (CPLX)
+          __stcs(p.cplx + ((size_t)q * p.wy + kyw) * p.wx + kxw, cmul(v, cmul(ox, ldg2(p.oy + kyw))));
+      }
+    }
+  });
+}
+
 // Column item: window columns [item*BC, item*BC + BC) of frame d.f.  The stage
 // buffer holds the band [NY][BC] copied from the scratch slot; the first DFT
 // pass writes back in place (up to the row-pair swap of col_row), the second
@@ -262,29 +299,18 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
   });
   if constexpr (AF) {
     // axial-first order: the column DFT completes V of bin q; write |V|^2 |K|^2
-    // (or |V| |K|) and optionally V with the output chirp and K
+    // (or |V| |K|) and optionally V with the output chirp and K.  The two
+    // options are tested once per item, not per value: tested inside the
+    // unrolled loop they were predicated on every value.
     const int kxw = d.item * BC + b;  // column bands already span the window's columns
     if (kxw < p.wx) {
-      const int q = af_bin(d.f, p.nl);
-      float* vdst = p.vol + (size_t)q * p.wy * p.wx + kxw;
-      float2 ox = make_float2(0.f, 0.f);
-      if (p.cplx) ox = ldg2(p.ox + kxw);
-      static_for<0, N2 / N1>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        const int k2 = j1 + N1 * i;
-#pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const int kyw = k2 + N2 * k1 - (FW ? 0 : p.y0);
-          if (FW || (kyw >= 0 && kyw < p.wy)) {
-            const float2 v = a[i * N1 + k1];
-            float pw = fmaf(v.x, v.x, v.y * v.y) * p.power_scale;
-            if (p.magnitude) pw = sqrtf(pw);
-            __stcs(vdst + (size_t)kyw * p.wx, pw);
-            if (p.cplx)
-              __stcs(p.cplx + ((size_t)q * p.wy + kyw) * p.wx + kxw, cmul(v, cmul(ox, ldg2(p.oy + kyw))));
-          }
-        }
-      });
+      if (p.cplx) {
+        if (p.magnitude) af_epilogue<NY, FW, true, true>(p, d, a, j1, kxw);
+        else af_epilogue<NY, FW, false, true>(p, d, a, j1, kxw);
+      } else {
+        if (p.magnitude) af_epilogue<NY, FW, true, false>(p, d, a, j1, kxw);
+        else af_epilogue<NY, FW, false, false>(p, d, a, j1, kxw);
+      }
     }
   } else {
     const int kxw = d.item * BC + b;
