@@ -11,6 +11,8 @@
 // volume per depth bin.  Sweeps of 64 to 256 frames take the persistent
 // streaming form (axial_stream_kernel: TMA-fed ring of stage buffers, two
 // consumer groups per SM); the others one CTA per tile (axial_kernel).
+#include <cuda.h>
+
 #include "fft_common.cuh"
 #include "mbarrier.cuh"
 
@@ -286,6 +288,208 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(co
   });
 }
 
+// ---------------------------------------------------------------- axial-first pass, tiled form
+//
+// Same output as rescale_axial_kernel for sweeps of 64, 128 and 256 frames, with
+// the frames read once and the real input used twice over:
+//  * a tile is 64 consecutive pixels of one sensor row (a 64-pixel strip x one
+//    row); pixels p and p + 32 are paired into one complex series
+//    z_t = u_t(p) + i u_t(p + 32), so 32 complex N_lambda-point DFTs give the
+//    64 real ones: X(p) = (Z_q + conj Z_{N-q}) / 2 and
+//    X(p + 32) = (Z_q - conj Z_{N-q}) / (2i);
+//  * every frame's two source rows of the tile (the rows of its y taps) are
+//    staged in shared memory by one 2D tensor copy per frame (TMA), which
+//    reads zeros outside the frame; the next tile's copies are issued as soon
+//    as the current tile's samples have been read, and land while it finishes
+//    its transform and writes its planes.  (16-byte cp.async copies of the
+//    same rows, ten per row, took 0.39 of 0.88 ms at 1024 x 1024 x 256);
+//  * the x taps of Eq. 5 follow u(x0 + k) = u(x0) + k s_t along the strip, so
+//    one record per (frame, strip), built in float64 (first staged column,
+//    integer and fractional part of u(x0) relative to it, s_t - 1), gives every
+//    pixel's taps: g = frac(u(x0)) + k (s_t - 1) in float32, column
+//    off + k + floor(g), weight g - floor(g); out-of-frame taps read the zero
+//    fill, as Eq. 5 is read here (taps outside the frame are 0).
+// The DFT over t is the axial kernel's two-stage split (N2-point DFTs in
+// registers, twiddle, exchange through shared memory, N1-point DFTs), its
+// second stage in place, so that the pair separation reads Z_{N-q} from the
+// same buffer after a barrier.
+struct RescaleAxialTileParams {
+  int ring_start;            // gate frame t is frame (ring_start + t) mod nl of the tensor map
+  const StripTap* xstrip;    // [nl][nx / 64]
+  const Tap* ytab;           // [nl][ny]
+  const float2* twl;         // [N2l][N1l], sign -
+  float2* planes;            // [nl/2 + 1][ny][nx]
+  int nx, ny, w;             // w: staged columns per source row (multiple of 8)
+  unsigned* err;             // kErrAxial is ORed in if a staging wait runs out
+};
+
+constexpr int kRaStrip = 64;  // pixels per tile (two per complex series)
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Eq. 5 at strip pixel k of a frame whose two staged source rows are r0, r1.
+__device__ __forceinline__ float ra_sample(int k, const StripTap& xs, const Tap& yt, const uint16_t* r0,
+                                           const uint16_t* r1) {
+  const float g = fmaf((float)k, xs.e, xs.f);
+  const float fl = floorf(g);
+  const float fr = g - fl;
+  const int col = xs.off + k + (int)fl;
+  const float a0 = __uint2float_rn(r0[col]), a1 = __uint2float_rn(r0[col + 1]);
+  const float b0 = __uint2float_rn(r1[col]), b1 = __uint2float_rn(r1[col + 1]);
+  const float h0 = fmaf(fr, a1 - a0, a0), h1 = fmaf(fr, b1 - b0, b0);
+  return fmaf(yt.w0, h0, yt.w1 * h1);
+}
+
+template <int NL>
+struct RaTile {
+  static constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  static constexpr int kThreads = 32 * N1;
+  // shared memory: exchange [NL][32] complex, strip records [NL], y taps [NL],
+  // twiddles [NL], then frame t's two staged rows (2 x w uint16) at t * stride,
+  // then the staging mbarrier.  A tensor copy's shared-memory destination must
+  // be 128-byte aligned: the staged rows start on a 128-byte boundary and each
+  // frame's block is padded to a multiple of 128 bytes.
+  static constexpr size_t kStageOffset = (size_t)NL * 32 * sizeof(float2) +
+                                         (size_t)NL * (sizeof(StripTap) + sizeof(Tap) + sizeof(float2));
+  static_assert(kStageOffset % 128 == 0, "staged rows on a 128-byte boundary");
+  __host__ __device__ static size_t frame_stride(int w) { return ((size_t)2 * w * sizeof(uint16_t) + 127) / 128 * 128; }
+  static size_t smem_bytes(int w) { return kStageOffset + (size_t)NL * frame_stride(w) + sizeof(uint64_t); }
+};
+
+template <int NL>
+__global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
+    rescale_axial_tile_kernel(const __grid_constant__ RescaleAxialTileParams p,
+                              const __grid_constant__ CUtensorMap fmap) {
+  using R = RaTile<NL>;
+  constexpr int N1 = R::N1, N2 = R::N2, T = R::kThreads;
+  static_assert(N2 % N1 == 0, "the second stage needs N1 | N2");
+  static_assert(T >= NL, "one loader thread per frame");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float2* ex = reinterpret_cast<float2*>(smem);
+  StripTap* xsm = reinterpret_cast<StripTap*>(ex + NL * 32);
+  Tap* ysm = reinterpret_cast<Tap*>(xsm + NL);
+  float2* tw = reinterpret_cast<float2*>(ysm + NL);
+  unsigned char* st = smem + R::kStageOffset;  // frame t's rows at st + t * fstride
+  const size_t fstride = R::frame_stride(p.w);
+  uint64_t& full = *reinterpret_cast<uint64_t*>(st + NL * fstride);
+  const int tid = threadIdx.x;
+  const int pp = tid % 32, j1 = tid / 32;
+  const int w = p.w;
+  const int strips = p.nx / kRaStrip;
+  const int ntiles = strips * p.ny;
+  const size_t plane = (size_t)p.ny * p.nx;
+  for (int i = tid; i < NL; i += T) tw[i] = p.twl[i];
+  if (tid == 0) {
+    mbar_init(&full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // loader role: thread t < NL stages frame t's two source rows of a tile
+  const bool loader = tid < NL;
+  const int frow = loader ? ((p.ring_start + tid) % NL) * p.ny : 0;  // first row of frame t in the map
+  const unsigned tile_bytes = (unsigned)(NL * 2 * w * sizeof(uint16_t));
+  auto stage = [&](const StripTap& xr, const Tap& yr) {
+    if (tid == 0) mbar_arrive_tx(&full, tile_bytes);
+    if (loader) {
+      xsm[tid] = xr;
+      ysm[tid] = yr;
+      // earlier generic reads of the buffer come before this async-proxy write
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      unsigned char* dst = st + (size_t)tid * fstride;
+      // a tensor copy needs a 128-byte aligned destination and an x start whose
+      // byte offset is a multiple of 16; a copy that would break either is not
+      // issued (the wait for it then runs out and reports kErrAxial)
+      if ((smem_u32(dst) & 127u) == 0u && (xr.xs & 7) == 0)
+        tma_load_2d(dst, &fmap, xr.xs, frow + yr.base, &full);
+      else
+        atomicOr(p.err, kErrAxial);
+    }
+  };
+  auto records = [&](int tile, StripTap& xr, Tap& yr) {
+    if (loader && tile < ntiles) {
+      const int strip = tile / p.ny, y = tile - strip * p.ny;
+      xr = p.xstrip[(size_t)tid * strips + strip];
+      yr = p.ytab[(size_t)tid * p.ny + y];
+    }
+  };
+  StripTap xr{};
+  Tap yr{};
+  int tile = blockIdx.x;
+  unsigned phase = 0;     // tiles staged and consumed so far
+  bool pending = false;   // a staging copy is in flight on `full`
+  records(tile, xr, yr);
+  if (tile < ntiles) {
+    stage(xr, yr);
+    pending = true;
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    records(next, xr, yr);  // in flight while this tile is transformed
+    const bool ok = mbar_wait_bounded(&full, phase & 1u, kAxWaitNs);
+    if (!ok && tid == 0) atomicOr(p.err, kErrAxial);
+    // this tile's rows and records are in; every thread is done with the last tile
+    if (__syncthreads_or(!ok)) break;
+    pending = false;
+    ++phase;
+    const int strip = tile / p.ny, y = tile - strip * p.ny;
+    // 1. Eq. 5 samples of frames t = j1 + N1 j2 at pixels pp and pp + 32 (one
+    //    complex series), N2-point DFT over j2, twiddle, exchange
+    float2 a[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) {
+      const int t = j1 + N1 * j2;
+      const StripTap xs = xsm[t];
+      const Tap yt = ysm[t];
+      const uint16_t* r0 = reinterpret_cast<const uint16_t*>(st + (size_t)t * fstride);
+      a[j2] = make_float2(ra_sample(pp, xs, yt, r0, r0 + w), ra_sample(pp + 32, xs, yt, r0, r0 + w));
+    }
+    Dft<N2, -1>::template run<1, 0>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) ex[(k2 * N1 + j1) * 32 + pp] = cmul(a[k2], tw[k2 * N1 + j1]);
+    __syncthreads();  // the staged rows are read: the next tile's copies may overwrite them
+    if (next < ntiles) {
+      stage(xr, yr);
+      pending = true;
+    }
+    // 2. N1-point DFTs, results back into the slots just read: Z_q, q = k2 + N2 k1,
+    //    at row k2 N1 + k1
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const int k2 = j1 + N1 * i;
+#pragma unroll
+      for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * 32 + pp];
+      Dft<N1, -1>::template run<1, i * N1>(a);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) ex[(k2 * N1 + k1) * 32 + pp] = a[i * N1 + k1];
+    });
+    __syncthreads();
+    // 3. the two real series' spectra, bins q = 0 .. NL/2, as plane rows
+    float2* dst = p.planes + (size_t)y * p.nx + strip * kRaStrip + pp;
+    static_for<0, N2 / N1>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const int k2 = j1 + N1 * i;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int q = k2 + N2 * k1;
+        if (q <= NL / 2) {
+          const int qm = (NL - q) % NL;
+          const float2 zq = a[i * N1 + k1];
+          const float2 zm = ex[((qm % N2) * N1 + qm / N2) * 32 + pp];
+          __stcs(dst + (size_t)q * plane, make_float2(0.5f * (zq.x + zm.x), 0.5f * (zq.y - zm.y)));
+          __stcs(dst + (size_t)q * plane + 32, make_float2(0.5f * (zq.y + zm.y), 0.5f * (zm.x - zq.x)));
+        }
+      }
+    });
+  }
+  // after a time-out, the copy still in flight lands before the CTA exits
+  if (pending && tid == 0 && !mbar_wait_bounded(&full, phase & 1u, kAxWaitNs)) atomicOr(p.err, kErrAxial);
+}
+
 struct GateCutsParams {
   const float2* inter;   // [wy][ntx][nl][32]
   const float2* wq;      // [nl] exp(-2 pi i k / nl)
@@ -441,6 +645,20 @@ cudaError_t launch_ra(const RescaleAxialParams& rp, cudaStream_t s) {
 }
 
 template <int NL>
+cudaError_t launch_ra_tiles(const RescaleAxialTileParams& rp, const CUtensorMap& fmap, int num_sms, cudaStream_t s) {
+  using R = RaTile<NL>;
+  const size_t smem = R::smem_bytes(rp.w);
+  cudaError_t e = cudaFuncSetAttribute(rescale_axial_tile_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (long long)(rp.nx / kRaStrip) * rp.ny;
+  long long grid = num_sms > 0 ? num_sms : 1;
+  if (grid > ntiles) grid = ntiles;
+  rescale_axial_tile_kernel<NL><<<(unsigned)grid, R::kThreads, smem, s>>>(rp, fmap);
+  return cudaGetLastError();
+}
+
+template <int NL>
 cudaError_t launch_stream(const AxialParams& ap, int num_sms, cudaStream_t s) {
   using S = AxStream<NL>;
   const size_t smem = (size_t)S::kStages * S::kTileBytes;
@@ -517,8 +735,37 @@ cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, f
   return cudaErrorInvalidValue;
 }
 
+bool rescale_axial_tiled(int nx, int nl) {
+  return nx % kRaStrip == 0 && (nl == 64 || nl == 128 || nl == 256);
+}
+
+size_t rescale_axial_tile_smem(int nl, int w) {
+  if (nl == 64) return RaTile<64>::smem_bytes(w);
+  if (nl == 128) return RaTile<128>::smem_bytes(w);
+  if (nl == 256) return RaTile<256>::smem_bytes(w);
+  return 0;
+}
+
 cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring_start, float2* planes,
                                  cudaStream_t s) {
+  if (p.ra_w > 0) {
+    alignas(64) CUtensorMap fmap;
+    if (!encode_frames_map(p, frames, p.ra_w, &fmap)) return cudaErrorInvalidValue;
+    RescaleAxialTileParams tp;
+    tp.ring_start = ring_start;
+    tp.xstrip = (const StripTap*)(p.ws + p.off_xstrip);
+    tp.ytab = (const Tap*)(p.ws + p.off_ytab);
+    tp.twl = (const float2*)(p.ws + p.off_twl);
+    tp.planes = planes;
+    tp.nx = p.nx;
+    tp.ny = p.ny;
+    tp.w = p.ra_w;
+    tp.err = &((Counters*)(p.ws + p.off_ctr))->err;
+    if (p.nl == 64) return launch_ra_tiles<64>(tp, fmap, p.num_sms, s);
+    if (p.nl == 128) return launch_ra_tiles<128>(tp, fmap, p.num_sms, s);
+    if (p.nl == 256) return launch_ra_tiles<256>(tp, fmap, p.num_sms, s);
+    return cudaErrorInvalidValue;
+  }
   RescaleAxialParams rp;
   rp.frames = frames;
   rp.ring_start = ring_start;

@@ -31,6 +31,17 @@ struct __align__(16) Tap {
   float pad;
 };
 
+// Eq. 5 along a 64-pixel strip x0 .. x0 + 63 of one frame (axial-first order):
+// the position u(x0 + k) = u(x0) + k s_t lies at staged column
+// off + k + floor(f + k e) with weight frac(f + k e), where the strip's source
+// rows are staged from column xs (a multiple of 8) on.  Built in float64.
+struct __align__(16) StripTap {
+  int xs;    // first staged source column (multiple of 8; may be negative)
+  int off;   // floor(u(x0)) - xs (>= 1)
+  float f;   // u(x0) - floor(u(x0))
+  float e;   // s_t - 1
+};
+
 // Device work-queue counters of the lateral kernel (zeroed before each launch).
 struct Counters {
   unsigned ticket;
@@ -194,6 +205,11 @@ struct Plan {
   // rescaled frames), then the lateral kernel on the planes
   bool axial_first = false;
   size_t off_aplanes = 0;
+  // tiled first pass (rescale_axial_tiled): strip records [nl][nx / 64] and the
+  // staged columns per source row (0: the one-tile-per-CTA kernel instead)
+  std::vector<StripTap> xstrip;
+  size_t off_xstrip = 0;
+  int ra_w = 0;
   char* ws = nullptr;
   int device = -1;
   int noalloc_device = -1;   // device of the plan's last no-allocation call (-1: none)
@@ -240,6 +256,13 @@ cudaError_t launch_xy_slide(const Plan& p, int slot0, int k, int z0, float sign,
 // the sweep at every pixel, bins 0..nl/2 written as planes [nl/2 + 1][ny][nx].
 cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring_start, float2* planes,
                                  cudaStream_t s);
+// The tiled first pass: sizes it is built for, and its dynamic shared memory
+// for w staged columns per source row.
+bool rescale_axial_tiled(int nx, int nl);
+size_t rescale_axial_tile_smem(int nl, int w);
+// Tensor map over a gate's frames seen as uint16 [nl * ny][nx], boxes of
+// box_cols columns x 2 rows (zero fill outside the frame).
+bool encode_frames_map(const Plan& p, const uint16_t* frames, int box_cols, void* map_out);
 bool lateral_supported(int nx, int ny);
 bool axial_supported(int nl);
 // Tensor-core axial kernel (axial_tc.cu): sweep lengths it handles, its DFT

@@ -152,6 +152,19 @@ bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out) {
 }
 
 
+bool encode_frames_map(const Plan& p, const uint16_t* frames, int box_cols, void* map_out) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)p.nx, (cuuint64_t)p.nl * p.ny};
+  cuuint64_t strides[1] = {(cuuint64_t)p.nx * sizeof(uint16_t)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, 2};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                   const_cast<uint16_t*>(frames), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 }  // namespace ssoct
 
 extern "C" {
@@ -223,6 +236,37 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
     const double s = lambda_m[t] / p.lambda1;
     for (int i = 0; i < nx; ++i) p.xtab[(size_t)t * nx + i] = make_tap(i, nx, s);
     for (int j = 0; j < ny; ++j) p.ytab[(size_t)t * ny + j] = make_tap(j, ny, s);
+  }
+  // Axial-first order, tiled first pass: one strip record per (frame, 64-pixel
+  // strip), and the staged width that holds every frame's taps of a strip
+  // (one column of slack at each end for the float32 position's rounding).
+  if (p.axial_first && !generic && rescale_axial_tiled(nx, nlambda)) {
+    const int strips = nx / 64;
+    p.xstrip.resize((size_t)nlambda * strips);
+    int wmax = 0;
+    const double c = nx / 2.0;
+    for (int t = 0; t < nlambda; ++t) {
+      const double s = lambda_m[t] / p.lambda1;
+      for (int k = 0; k < strips; ++k) {
+        const double u0 = c + (64.0 * k - c) * s;
+        const double u1 = c + (64.0 * k + 63.0 - c) * s;
+        const long n0 = (long)std::floor(u0);
+        const long xs = (long)std::floor((double)(n0 - 1) / 8.0) * 8;
+        StripTap& r = p.xstrip[(size_t)t * strips + k];
+        r.xs = (int)xs;
+        r.off = (int)(n0 - xs);
+        r.f = (float)(u0 - (double)n0);
+        r.e = (float)(s - 1.0);
+        const long hi = (long)std::floor(u1) + 1 - xs;  // last staged column the strip reads
+        wmax = std::max<int>(wmax, (int)std::max<long>(hi + 2, r.off + 2));
+      }
+    }
+    const int w = (wmax + 7) / 8 * 8;
+    // beyond 128 columns (rescale ratios far from 1) the staging buffer would not
+    // fit, and the one-tile-per-CTA kernel is used
+    const bool ok = w <= 128 && rescale_axial_tile_smem(nlambda, w) <= 227u * 1024u;
+    if (ok) p.ra_w = w;
+    else p.xstrip.clear();
   }
   // Eq. 6 chirps.  alpha x (k - n/2)^2 is the chirp phase / pi.
   p.cx = input_chirp(nx, p.alpha);
@@ -302,6 +346,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
   if (generic) p.off_cg = take(sizeof(float2) * (size_t)nx * ny);
   if (p.axial_first) p.off_aplanes = take(sizeof(float2) * (size_t)(nlambda / 2 + 1) * ny * nx);
+  if (p.ra_w) p.off_xstrip = take(sizeof(StripTap) * p.xstrip.size());
   if (!generic && !p.axial_first) p.off_xys = take(sizeof(float2) * (size_t)p.wy * p.ntx * kTile);
   if (generic || (flags & SSOCT_FLAG_PUPIL)) p.off_F = take(sizeof(float2) * (size_t)nlambda * ny * nx);
   if (flags & SSOCT_FLAG_PUPIL) {
@@ -363,6 +408,7 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
       {p.off_twl, p.twl.data(), sizeof(float2) * p.twl.size()},
       {p.off_tcb, p.tcb.data(), sizeof(unsigned short) * p.tcb.size()},
       {p.off_wq, p.wq.data(), sizeof(float2) * p.wq.size()},
+      {p.off_xstrip, p.xstrip.data(), sizeof(StripTap) * p.xstrip.size()},
   };
   for (const Up& u : ups) {
     if (!u.n) continue;

@@ -350,6 +350,22 @@ def test_axial_first_matches_oracle(ss, shape, window):
     print(f"axial-first {shape} window={window}: complex rel L2 {err:.3e}")
 
 
+@pytest.mark.parametrize("shape,window", [((64, 64, 64), None), ((128, 64, 128), (5, 9, 101, 50))])
+def test_axial_first_decreasing_sweep(ss, shape, window):
+    """A sweep from long to short wavelengths: every frame is rescaled by a ratio
+    below 1 (Eq. 5 shrinks the field instead of widening it), so the tiled first
+    pass staggers its taps the other way along each strip."""
+    nx, ny, nl = shape
+    w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=nx + ny + nl + 1)
+    lam = np.ascontiguousarray(w.lambdas[::-1])
+    plan = ss.Plan(nx, ny, nl, w.pitch, w.z, lam, window=window, flags=ss.SSOCT_FLAG_AXIAL_FIRST)
+    vol, cplx = plan.reconstruct(_dev(w.frames), complex_out=True)
+    plan.sync()
+    ref = oracle.reconstruct(w.frames, w.pitch, w.z, lam, window=window, method="fft")
+    err = _check(vol.cpu().numpy(), cplx.cpu().numpy(), ref, quadrant=False)
+    print(f"axial-first, decreasing sweep {shape} window={window}: complex rel L2 {err:.3e}")
+
+
 def test_axial_first_ring_magnitude_profile(ss):
     w = synth.workload("mid_512x512x128")
     af = ss.SSOCT_FLAG_AXIAL_FIRST
