@@ -465,6 +465,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
           kind = kEndItem;  // the buffer's old item is lost; the group still gets its end mark
           break;
         }
+        __nanosleep(32);  // leave the issue slots to the consumers meanwhile
       }
     }
     // 3. hand over
@@ -542,9 +543,11 @@ __device__ void publisher(const LateralParams& p, uint64_t* done_bar, Handover* 
     const int f = ho->f[s % kPubQ];
     const int b = (int)(s % kStages);
     const unsigned parity = (s / kStages) & 1u;
-    if (!mbar_test(&done_bar[b], parity)) {
+    // try_wait suspends the thread in hardware between checks: a test_wait spin
+    // here would take issue slots from the consumer warps of its scheduler
+    if (!mbar_try(&done_bar[b], parity)) {
       const unsigned long long t0 = global_timer_ns();
-      while (!mbar_test(&done_bar[b], parity)) {
+      while (!mbar_try(&done_bar[b], parity)) {
         if (global_timer_ns() - t0 > wait_limit) {
           give_up();
           return;
