@@ -369,7 +369,10 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
   constexpr int N1 = R::N1, N2 = R::N2, T = R::kThreads;
   static_assert(N2 % N1 == 0, "the second stage needs N1 | N2");
   static_assert(T >= NL, "one loader thread per frame");
-  extern __shared__ __align__(1024) unsigned char smem[];
+  // its own name: the other kernels of this file declare the dynamic shared
+  // memory with 16-byte alignment, and a tensor copy needs 128 here
+  extern __shared__ __align__(1024) unsigned char smem_ra[];
+  unsigned char* smem = smem_ra;
   float2* ex = reinterpret_cast<float2*>(smem);
   StripTap* xsm = reinterpret_cast<StripTap*>(ex + NL * 32);
   Tap* ysm = reinterpret_cast<Tap*>(xsm + NL);

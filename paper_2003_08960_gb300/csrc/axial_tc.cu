@@ -15,14 +15,18 @@
 // scaling is needed), and D = Ahi Bhi + Ahi Blo + Alo Bhi; the dropped Alo Blo
 // term and the rounding of lo put the relative error near 2^-16 per stage.
 //
-// One 256-thread CTA per 32-pixel tile of one window row (the sweep-axis
-// intermediate stores such a tile as 256 x 32 contiguous complex values): 4
-// blocks of 8 pixels, 24 MMAs per stage issued by one thread into 128 TMEM
-// columns, results read back with tcgen05.ld, |V|^2 staged in shared memory and
-// written as 128-byte rows of the volume.  70 KB of shared memory, 128 TMEM
-// columns and at most 80 registers per thread let three CTAs share an SM, so
-// that one CTA's loads overlap the others' conversions and MMAs; one thread
-// waits for the MMAs while the rest wait at the CTA barrier.
+// The kernel is persistent, one CTA per SM, fed like the FP32 streaming axial
+// kernel: whole tiles (256 x 32 complex values, contiguous in the sweep-axis
+// intermediate) arrive by 1D TMA bulk copies into a ring of three 64 KB
+// shared-memory buffers, a ring's worth ahead, and two groups of 16 warps
+// compute the CTA's tiles g, g + 2, ...  A tile never leaves its buffer: the
+// FP32 values are read into registers and written back as the BF16 hi / lo
+// stage-1 operands (the same 64 KB), the stage-2 operands overwrite those once
+// the stage-1 MMAs are done, and the |V|^2 rows overwrite those once the
+// stage-2 MMAs are done.  Each group owns 128 TMEM columns (4 blocks x N = 32
+// fp32 accumulators), one thread issues its 24 MMAs per stage and waits on its
+// commit barrier, and while one group waits for its MMAs or its next tile the
+// other computes.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -30,16 +34,23 @@
 #include <vector>
 
 #include "fft_common.cuh"
+#include "mbarrier.cuh"
 
 namespace ssoct {
 namespace {
 
-constexpr int kTcThreads = 256;
 constexpr int kTcN = 256;          // sweep length this kernel is built for
 constexpr int kTcR = 16;           // radix of both stages
 constexpr int kTcBlocks = 4;       // 8-pixel M blocks per 32-pixel tile
 constexpr int kTcK = 2 * kTcR;     // 32: real + imaginary parts
-constexpr unsigned kTcCols = kTcBlocks * kTcK;  // TMEM columns (fp32 accumulators)
+constexpr int kTcGroups = 2;       // tiles computed at once per CTA
+constexpr int kTcGroupThreads = 512;
+constexpr int kTcThreads = kTcGroups * kTcGroupThreads;
+constexpr unsigned kTcCols = kTcBlocks * kTcK;  // TMEM columns (fp32 accumulators) per group
+constexpr int kTcStages = 3;                    // ring buffers
+constexpr int kTcFull = 6;                      // full barriers: tile mod lcm(stages, groups)
+constexpr size_t kTcTileBytes = (size_t)kTcN * kTile * sizeof(float2);  // 64 KB
+constexpr unsigned long long kTcLoadWaitNs = 4000000000ull;
 constexpr unsigned long long kTcWaitNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -95,7 +106,7 @@ __device__ __forceinline__ void tc_ld32(unsigned taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(u[i]);
 }
 // Bounded wait for an mbarrier phase (true on completion).
-__device__ bool tc_wait(uint64_t* bar, unsigned parity) {
+__device__ bool tc_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns = kTcWaitNs) {
   const unsigned long long t0 = global_timer_ns();
   for (;;) {
     unsigned ok;
@@ -105,7 +116,7 @@ __device__ bool tc_wait(uint64_t* bar, unsigned parity) {
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (global_timer_ns() - t0 > kTcWaitNs) return false;
+    if (global_timer_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -128,7 +139,7 @@ struct TcParams {
   int wx, wy, ntx;
   float power_scale;
   int magnitude;
-  unsigned* err;                // set to 1 if a wait ran out
+  unsigned* err;                // kErrAxialTc (MMA wait) / kErrAxial (tile wait) ORed in on a time-out
 };
 
 __device__ __forceinline__ void split2_bf16(float a, float b, unsigned& hi, unsigned& lo) {
@@ -143,110 +154,186 @@ __device__ __forceinline__ void split2_bf16(float a, float b, unsigned& hi, unsi
 // i * 8 + pl keeps a warp's 32 pixels on distinct 16-byte slots of a core matrix.
 __device__ __forceinline__ int tc_row(int i, int pl) { return i * 8 + pl; }
 
-__global__ void __launch_bounds__(kTcThreads, 3) axial_tc_kernel(const __grid_constant__ TcParams p) {
+// Barrier of one group (named barrier 1 + g, 512 threads); returns the OR of v.
+__device__ __forceinline__ bool tc_group_sync_or(int g, bool v) {
+  unsigned r;
+  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+               : "=r"(r)
+               : "r"((unsigned)v), "r"(1 + g), "n"(kTcGroupThreads)
+               : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void tc_group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kTcGroupThreads) : "memory");
+}
+
+constexpr int kABlock = 128 * kTcK;  // elements of one M block of an operand
+constexpr int kOutStride = 40;       // floats per |V|^2 row in the buffer; conflict-free both ways
+
+// Copy of the CTA's tile t (global tile blockIdx.x + t * gridDim.x) into ring buffer t mod kTcStages.
+__device__ __forceinline__ void tc_fill(const TcParams& p, unsigned char* ring, uint64_t* full, unsigned* fills, int t) {
+  const int f = t % kTcFull;
+  ++fills[f];
+  mbar_arrive_tx(&full[f], (unsigned)kTcTileBytes);
+  const size_t gt = blockIdx.x + (size_t)t * gridDim.x;
+  tma_load_1d(ring + (size_t)(t % kTcStages) * kTcTileBytes, p.inter + gt * kTcN * kTile, (unsigned)kTcTileBytes,
+              &full[f]);
+}
+
+// 24 MMAs of one stage: D[blk] = Ahi Bhi + Ahi Blo + Alo Bhi, K = 32 as two K = 16 steps.
+__device__ __forceinline__ void tc_issue_stage(unsigned tmem, const unsigned short* A, const unsigned short* Bs,
+                                               uint64_t* bar) {
+  const unsigned idesc = tc_idesc(128, kTcK);
+#pragma unroll 1
+  for (int blk = 0; blk < kTcBlocks; ++blk) {
+    const unsigned short* a_terms[3] = {A + blk * kABlock, A + blk * kABlock, A + (kTcBlocks + blk) * kABlock};
+    const unsigned short* b_terms[3] = {Bs, Bs + kTcK * kTcK, Bs};
+    bool acc = false;
+#pragma unroll
+    for (int term = 0; term < 3; ++term)
+#pragma unroll
+      for (int ks = 0; ks < kTcK / 16; ++ks) {
+        tc_mma(tmem + (unsigned)(blk * kTcK), tc_desc(a_terms[term] + ks * 2 * 64), tc_desc(b_terms[term] + ks * 2 * 64),
+               idesc, acc);
+        acc = true;
+      }
+  }
+  tc_commit(bar);
+}
+
+// |V|^2 |K|^2 (|V| |K| if MAG) of the 16 depth bins q = k2 + 16 k1 this thread
+// holds into the tile's output rows; with CPLX also V with the output chirp and K.
+template <bool MAG, bool CPLX>
+__device__ __forceinline__ void tc_epilogue(const TcParams& p, const float (&v)[32], float* out, int k2, int px,
+                                            int kx0, int kyw) {
+  const bool in = kx0 + px < p.wx;
+  float2 of = make_float2(0.f, 0.f);
+  if constexpr (CPLX) {
+    if (in) of = cmul(ldg2(p.ox + kx0 + px), ldg2(p.oy + kyw));
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    const int q = k2 + 16 * k1;
+    const float2 x = make_float2(v[k1], v[16 + k1]);
+    float pw = fmaf(x.x, x.x, x.y * x.y) * p.power_scale;
+    if constexpr (MAG) pw = sqrtf(pw);
+    out[q * kOutStride + px] = pw;
+    if constexpr (CPLX) {
+      if (in) __stcs(p.cplx + ((size_t)q * p.wy + kyw) * p.wx + kx0 + px, cmul(x, of));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // A operands: [hi / lo][block][128 x 32] BF16; the |V|^2 tile reuses them
-  unsigned short* A = reinterpret_cast<unsigned short*>(smem);
-  constexpr int kABlock = 128 * kTcK;                        // elements per block
-  unsigned short* Bs = A + 2 * kTcBlocks * kABlock;          // [hi / lo][32 x 32]
-  float2* tw = reinterpret_cast<float2*>(Bs + 2 * kTcK * kTcK);
-  constexpr int kOutStride = 40;                             // floats; conflict-free both ways
-  float* out = reinterpret_cast<float*>(smem);               // [256][kOutStride] after stage 2
-  __shared__ __align__(8) uint64_t bar;
+  unsigned char* ring = smem;                                                      // [3][64 KB]
+  unsigned short* Bs = reinterpret_cast<unsigned short*>(ring + kTcStages * kTcTileBytes);  // [hi / lo][32 x 32]
+  float2* tw = reinterpret_cast<float2*>(Bs + 2 * kTcK * kTcK);                    // [256]
+  __shared__ __align__(8) uint64_t full[kTcFull];
+  __shared__ __align__(8) uint64_t mma_bar[kTcGroups];
+  __shared__ unsigned fills[kTcFull];
   __shared__ unsigned tmem_base;
-  __shared__ int ok_flag;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int tile = blockIdx.x, kyw = blockIdx.y;
+  const int ntiles = p.ntx * p.wy;
+  const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                 "n"(kTcCols)
+                 "n"(kTcGroups * kTcCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+    for (int f = 0; f < kTcFull; ++f) {
+      mbar_init(&full[f], 1);
+      fills[f] = 0u;
+    }
+    for (int g = 0; g < kTcGroups; ++g) mbar_init(&mma_bar[g], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int t = 0; t < kTcStages && t < mine; ++t) tc_fill(p, ring, full, fills, t);
   }
-  reinterpret_cast<uint4*>(Bs)[tid] = __ldg(reinterpret_cast<const uint4*>(p.bmat) + tid);  // 4 KB
-  tw[tid] = ldg2(p.twl + tid);                                                             // 256 twiddles
-
-  // 1. t = j1 + 16 j2 -> stage-1 row (pixel, j1), K = j2 (real) / 16 + j2 (imaginary).
-  //    Work unit c = (j1, half of j2): 8 coalesced loads, 4 16-byte stores.
-  {
-    const float2* src = p.inter + ((size_t)kyw * p.ntx + tile) * kTcN * kTile + lane;
-    const int blk = lane >> 3, pl = lane & 7;
-    unsigned short* Ahi = A + blk * kABlock;
-    unsigned short* Alo = A + (kTcBlocks + blk) * kABlock;
-#pragma unroll 2
-    for (int c = warp; c < 2 * kTcR; c += kTcThreads / 32) {
-      const int j1 = c & 15, h = c >> 4;
-      float2 x[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) x[i] = __ldcs(src + (j1 + 16 * (8 * h + i)) * kTile);
-      uint4 hr, lr, hm, lm;
-      split2_bf16(x[0].x, x[1].x, hr.x, lr.x);
-      split2_bf16(x[2].x, x[3].x, hr.y, lr.y);
-      split2_bf16(x[4].x, x[5].x, hr.z, lr.z);
-      split2_bf16(x[6].x, x[7].x, hr.w, lr.w);
-      split2_bf16(x[0].y, x[1].y, hm.x, lm.x);
-      split2_bf16(x[2].y, x[3].y, hm.y, lm.y);
-      split2_bf16(x[4].y, x[5].y, hm.z, lm.z);
-      split2_bf16(x[6].y, x[7].y, hm.w, lm.w);
-      const int r = tc_row(j1, pl);
-      *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 8 * h)) = hr;
-      *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 8 * h)) = lr;
-      *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 16 + 8 * h)) = hm;
-      *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 16 + 8 * h)) = lm;
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (tid < 256) reinterpret_cast<uint4*>(Bs)[tid] = __ldg(reinterpret_cast<const uint4*>(p.bmat) + tid);  // 4 KB
+  if (tid < kTcN) tw[tid] = ldg2(p.twl + tid);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const unsigned tmem = tmem_base;
-  const unsigned idesc = tc_idesc(128, kTcK);
-  // D = Ahi Bhi + Ahi Blo + Alo Bhi for each block, K = 32 as two K = 16 steps
-  auto issue_stage = [&]() {
-#pragma unroll 1
-    for (int blk = 0; blk < kTcBlocks; ++blk) {
-      const unsigned short* a_terms[3] = {A + blk * kABlock, A + blk * kABlock, A + (kTcBlocks + blk) * kABlock};
-      const unsigned short* b_terms[3] = {Bs, Bs + kTcK * kTcK, Bs};
-      bool acc = false;
-#pragma unroll
-      for (int term = 0; term < 3; ++term)
-#pragma unroll
-        for (int ks = 0; ks < kTcK / 16; ++ks) {
-          tc_mma(tmem + (unsigned)(blk * kTcK), tc_desc(a_terms[term] + ks * 2 * 64), tc_desc(b_terms[term] + ks * 2 * 64),
-                 idesc, acc);
-          acc = true;
-        }
-    }
-    tc_commit(&bar);
-  };
-  if (tid == 0) {
-    issue_stage();
-    ok_flag = tc_wait(&bar, 0) ? 1 : 0;
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const bool ok1 = ok_flag != 0;
+  const int g = tid / kTcGroupThreads;
+  const int lt = tid % kTcGroupThreads;
+  const int gw = lt / 32;                       // warp within the group (0..15)
+  const int quad = gw & 3, qblk = gw >> 2;      // TMEM lane quadrant, M block read by this warp
+  const unsigned tmem = tmem_base + (unsigned)(g * kTcCols);
+  for (int i = g, prev = -1;; prev = i, i += kTcGroups) {
+    tc_group_sync(g);  // every thread of the group is done with tile prev's buffer
+    if (lt == 0 && prev >= 0 && prev + kTcStages < mine) tc_fill(p, ring, full, fills, prev + kTcStages);
+    if (i >= mine) break;
+    const bool ok0 = tc_wait(&full[i % kTcFull], (unsigned)(i / kTcFull) & 1u, kTcLoadWaitNs);
+    if (!ok0 && lt == 0) atomicOr(p.err, kErrAxial);
+    if (tc_group_sync_or(g, !ok0)) break;
+    unsigned char* buf = ring + (size_t)(i % kTcStages) * kTcTileBytes;
+    unsigned short* A = reinterpret_cast<unsigned short*>(buf);  // [hi / lo][block][128 x 32]
+    const int gt = (int)blockIdx.x + i * (int)gridDim.x;
+    const int kyw = gt / p.ntx;
+    const int kx0 = (gt - kyw * p.ntx) * kTile;
 
-  // 2. twiddle w256^(j1 k2) and re-layout as the stage-2 operand: row (pixel, k2),
-  //    K = j1 (real) / 16 + j1 (imaginary).  Warp quadrant quad holds TMEM lanes
-  //    32 quad .. 32 quad + 31, i.e. j1 = 4 quad + lane / 8 of each block.
-  const int quad = warp & 3;
-  if (ok1) {
-#pragma unroll 1
-    for (int hblk = 0; hblk < 2; ++hblk) {
-      const int blk = (warp >> 2) + 2 * hblk;
-      float v[32];
-      tc_ld32(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(blk * kTcK), v);
-      const int r = quad * 32 + lane;
-      const int j1 = r >> 3, pl = r & 7;
+    // 1. t = j1 + 16 j2 -> stage-1 row (pixel, j1), K = j2 (real) / 16 + j2 (imaginary).
+    //    Work units c = (j1, half of j2), two per warp; all values are read
+    //    before any operand is written over them.
+    {
+      const float2* src = reinterpret_cast<const float2*>(buf) + lane;
+      float2 x[2][8];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = gw + 16 * u, j1 = c & 15, h = c >> 4;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[u][k] = src[(j1 + 16 * (8 * h + k)) * kTile];
+      }
+      tc_group_sync(g);
+      const int blk = lane >> 3, pl = lane & 7;
       unsigned short* Ahi = A + blk * kABlock;
       unsigned short* Alo = A + (kTcBlocks + blk) * kABlock;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = gw + 16 * u, j1 = c & 15, h = c >> 4;
+        uint4 hr, lr, hm, lm;
+        split2_bf16(x[u][0].x, x[u][1].x, hr.x, lr.x);
+        split2_bf16(x[u][2].x, x[u][3].x, hr.y, lr.y);
+        split2_bf16(x[u][4].x, x[u][5].x, hr.z, lr.z);
+        split2_bf16(x[u][6].x, x[u][7].x, hr.w, lr.w);
+        split2_bf16(x[u][0].y, x[u][1].y, hm.x, lm.x);
+        split2_bf16(x[u][2].y, x[u][3].y, hm.y, lm.y);
+        split2_bf16(x[u][4].y, x[u][5].y, hm.z, lm.z);
+        split2_bf16(x[u][6].y, x[u][7].y, hm.w, lm.w);
+        const int r = tc_row(j1, pl);
+        *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 8 * h)) = hr;
+        *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 8 * h)) = lr;
+        *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 16 + 8 * h)) = hm;
+        *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 16 + 8 * h)) = lm;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    tc_group_sync(g);
+    tc_fence_after();
+    bool ok = true;
+    if (lt == 0) {
+      tc_issue_stage(tmem, A, Bs, &mma_bar[g]);
+      ok = tc_wait(&mma_bar[g], 0u);
+      if (!ok) atomicOr(p.err, kErrAxialTc);
+    }
+    tc_fence_before();
+    const bool bad1 = tc_group_sync_or(g, !ok);
+    tc_fence_after();
+    if (bad1) break;
+
+    // 2. twiddle w256^(j1 k2) and re-layout as the stage-2 operand: row (pixel, k2),
+    //    K = j1 (real) / 16 + j1 (imaginary), over the stage-1 operand (its MMAs are done)
+    {
+      float v[32];
+      tc_ld32(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(qblk * kTcK), v);
+      const int r = quad * 32 + lane;
+      const int j1 = r >> 3, pl = r & 7;
+      unsigned short* Ahi = A + qblk * kABlock;
+      unsigned short* Alo = A + (kTcBlocks + qblk) * kABlock;
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
         const float2 z = cmul(make_float2(v[k2], v[16 + k2]), tw[k2 * 16 + j1]);
@@ -260,58 +347,59 @@ __global__ void __launch_bounds__(kTcThreads, 3) axial_tc_kernel(const __grid_co
         Alo[tc_core_off(r2, 16 + j1)] = lm;
       }
     }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (tid == 0) {
-    if (ok1) issue_stage();
-    ok_flag = (ok1 && tc_wait(&bar, 1)) ? 1 : 0;
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const bool ok2 = ok_flag != 0;
-
-  // 3. V[k2 + 16 k1] sits in row (pixel, k2), columns k1 (real) / 16 + k1 (imaginary)
-  const int kx0 = tile * kTile;
-#pragma unroll 1
-  for (int hblk = 0; hblk < 2; ++hblk) {
-    const int blk = (warp >> 2) + 2 * hblk;
-    float v[32];
-    if (ok2) tc_ld32(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(blk * kTcK), v);
-    else
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = 0.f;
-    const int r = quad * 32 + lane;
-    const int k2 = r >> 3, px = blk * 8 + (r & 7);
-    const bool in = kx0 + px < p.wx;
-    float2 of = make_float2(0.f, 0.f);
-    if (p.cplx && in) of = cmul(ldg2(p.ox + kx0 + px), ldg2(p.oy + kyw));
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) {
-      const int q = k2 + 16 * k1;
-      const float2 x = make_float2(v[k1], v[16 + k1]);
-      float pw = fmaf(x.x, x.x, x.y * x.y) * p.power_scale;
-      if (p.magnitude) pw = sqrtf(pw);
-      out[q * kOutStride + px] = pw;
-      if (p.cplx && in) __stcs(p.cplx + ((size_t)q * p.wy + kyw) * p.wx + kx0 + px, cmul(x, of));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    tc_group_sync(g);
+    tc_fence_after();
+    if (lt == 0) {
+      tc_issue_stage(tmem, A, Bs, &mma_bar[g]);
+      ok = tc_wait(&mma_bar[g], 1u);
+      if (!ok) atomicOr(p.err, kErrAxialTc);
     }
+    tc_fence_before();
+    const bool bad2 = tc_group_sync_or(g, !ok);
+    tc_fence_after();
+    if (bad2) break;
+
+    // 3. V[k2 + 16 k1] sits in row (pixel, k2), columns k1 (real) / 16 + k1
+    //    (imaginary); |V|^2 rows over the stage-2 operand (its MMAs are done)
+    float* out = reinterpret_cast<float*>(buf);  // [256][kOutStride]
+    {
+      float v[32];
+      tc_ld32(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(qblk * kTcK), v);
+      const int r = quad * 32 + lane;
+      const int k2 = r >> 3, px = qblk * 8 + (r & 7);
+      if (p.cplx) {
+        if (p.magnitude) tc_epilogue<true, true>(p, v, out, k2, px, kx0, kyw);
+        else tc_epilogue<false, true>(p, v, out, k2, px, kx0, kyw);
+      } else {
+        if (p.magnitude) tc_epilogue<true, false>(p, v, out, k2, px, kx0, kyw);
+        else tc_epilogue<false, false>(p, v, out, k2, px, kx0, kyw);
+      }
+    }
+    tc_group_sync(g);
+    // 4. 128-byte rows of the volume
+    if (kx0 + lane < p.wx) {
+      float* dst = p.vol + (size_t)kyw * p.wx + kx0 + lane;
+      const size_t plane = (size_t)p.wy * p.wx;
+#pragma unroll 4
+      for (int q = gw; q < kTcN; q += kTcGroupThreads / 32) __stcs(dst + (size_t)q * plane, out[q * kOutStride + lane]);
+    }
+    // this thread's accesses to the buffer come before its next TMA fill (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  __syncthreads();
-  // 4. 128-byte rows of the volume
-  if (kx0 + lane < p.wx) {
-    float* dst = p.vol + (size_t)kyw * p.wx + kx0 + lane;
-    const size_t plane = (size_t)p.wy * p.wx;
-#pragma unroll 8
-    for (int q = warp; q < kTcN; q += kTcThreads / 32) __stcs(dst + (size_t)q * plane, out[q * kOutStride + lane]);
-  }
-  if (tid == 0 && !ok2) atomicOr(p.err, kErrAxialTc);
+  // copies still in flight (after a time-out) land before the CTA exits; the
+  // last fill of each barrier is its latest phase
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcCols) : "memory");
+  if (tid == 0)
+    for (int f = 0; f < kTcFull; ++f)
+      if (fills[f] && !tc_wait(&full[f], (fills[f] - 1u) & 1u, kTcLoadWaitNs)) atomicOr(p.err, kErrAxial);
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "n"(kTcGroups * kTcCols)
+                 : "memory");
+  }
 }
 
 }  // namespace
@@ -319,7 +407,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) axial_tc_kernel(const __grid_co
 bool axial_tc_supported(int nl) { return nl == kTcN; }
 
 size_t axial_tc_smem_bytes() {
-  return (size_t)2 * kTcBlocks * 128 * kTcK * 2 + (size_t)2 * kTcK * kTcK * 2 + kTcN * sizeof(float2);
+  return (size_t)kTcStages * kTcTileBytes + (size_t)2 * kTcK * kTcK * 2 + kTcN * sizeof(float2);
 }
 
 size_t axial_tc_table_elems() { return 2 * kTcK * kTcK; }
@@ -359,7 +447,7 @@ void axial_tc_table(std::vector<unsigned short>& out) {
 }
 
 cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigned short* bmat, unsigned* err,
-                            cudaStream_t s) {
+                            int num_sms, cudaStream_t s) {
   TcParams p;
   p.inter = ap.inter;
   p.vol = ap.vol;
@@ -377,8 +465,11 @@ cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigne
   const size_t smem = axial_tc_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(axial_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(ap.ntx, ap.wy);
-  axial_tc_kernel<<<grid, kTcThreads, smem, s>>>(p);
+  const long long ntiles = (long long)ap.ntx * ap.wy;
+  long long grid = num_sms > 0 ? num_sms : 1;  // persistent: one CTA per SM
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) return cudaSuccess;
+  axial_tc_kernel<<<(unsigned)grid, kTcThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 

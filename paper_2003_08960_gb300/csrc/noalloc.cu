@@ -177,7 +177,7 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
   ap.power_scale = (float)(p.alpha * p.alpha);
   ap.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
   ap.err = &lp.ctr->err;
-  e = p.use_tc ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb), &lp.ctr->err, s)
+  e = p.use_tc ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb), &lp.ctr->err, num_sms, s)
                                       : launch_axial_with(p, ap, num_sms, s);
   if (e != cudaSuccess) return fail(p, SSOCT_ECUDA, std::string("axial kernel launch: ") + cudaGetErrorString(e));
   return SSOCT_OK;

@@ -272,7 +272,7 @@ bool axial_tc_supported(int nl);
 void axial_tc_table(std::vector<unsigned short>& out);
 size_t axial_tc_smem_bytes();
 cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigned short* bmat, unsigned* err,
-                            cudaStream_t s);
+                            int num_sms, cudaStream_t s);
 // Aberration path (sharpness.cu): sizes it compiles, the c P table, and the
 // forward + adjoint launches that leave loss and gradient in the FP64 block at
 // off_red ([0] S1, [1] S2, [2] loss, [3] dL/dz, [4..18] dL/dc_1..15).

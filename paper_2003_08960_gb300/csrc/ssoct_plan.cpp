@@ -569,7 +569,7 @@ static ssoct_status launch_axial_pass(Plan& p, float* vol, void* cplx, cudaStrea
   ap.err = &((Counters*)(ws + p.off_ctr))->err;
   cudaError_t e = p.use_tc
                       ? launch_axial_tc(p, ap, (const unsigned short*)(ws + p.off_tcb),
-                                        &((Counters*)(ws + p.off_ctr))->err, s)
+                                        &((Counters*)(ws + p.off_ctr))->err, p.num_sms, s)
                       : launch_axial(p, ap, s);
   if (e != cudaSuccess) return cuda_fail(&p, e, "axial kernel launch");
   if (ev) cudaEventRecord(ev[2], s);
