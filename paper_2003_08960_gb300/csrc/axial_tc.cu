@@ -9,8 +9,11 @@
 //   V[k2 + 16 k1] = sum_j1 Y'[j1][k2] w16^(j1 k1).
 // Each stage is a real GEMM D[M=128][N=32] = A[128][K=32] B[32][32]^T per block
 // of 8 pixels: rows are (pixel, j1) (stage 1) or (pixel, k2) (stage 2), the K
-// index runs over (real parts, imaginary parts) of the 16 inputs, and B is the
-// real 32 x 32 form of the complex 16-point DFT matrix.  Operands are split as
+// index runs over the 16 inputs with real and imaginary parts interleaved
+// (K = 2 j + 0 / 1), the N index likewise over the 16 outputs, and B is the
+// real 32 x 32 form of the complex 16-point DFT matrix in that order.  With
+// the parts interleaved, one packed BF16x2 split of a complex value gives the
+// two adjacent operand entries (hi and lo), stored with one 4-byte store each.  Operands are split as
 // x = hi + lo with hi, lo in BF16 (BF16 keeps FP32's exponent range, so no
 // scaling is needed), and D = Ahi Bhi + Ahi Blo + Alo Bhi; the dropped Alo Blo
 // term and the rounding of lo put the relative error near 2^-16 per stage.
@@ -120,13 +123,6 @@ __device__ bool tc_wait(uint64_t* bar, unsigned parity, unsigned long long limit
   }
 }
 
-// x = hi + lo, both BF16 (round to nearest even).
-__device__ __forceinline__ void split_bf16(float x, unsigned short& hi, unsigned short& lo) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-  hi = __bfloat16_as_ushort(h);
-  lo = __bfloat16_as_ushort(l);
-}
 
 struct TcParams {
   const float2* inter;          // [wy][ntx][256][32]
@@ -214,7 +210,7 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, const float (&v)[
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) {
     const int q = k2 + 16 * k1;
-    const float2 x = make_float2(v[k1], v[16 + k1]);
+    const float2 x = make_float2(v[2 * k1], v[2 * k1 + 1]);
     float pw = fmaf(x.x, x.x, x.y * x.y) * p.power_scale;
     if constexpr (MAG) pw = sqrtf(pw);
     out[q * kOutStride + px] = pw;
@@ -275,7 +271,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
     const int kyw = gt / p.ntx;
     const int kx0 = (gt - kyw * p.ntx) * kTile;
 
-    // 1. t = j1 + 16 j2 -> stage-1 row (pixel, j1), K = j2 (real) / 16 + j2 (imaginary).
+    // 1. t = j1 + 16 j2 -> stage-1 row (pixel, j1), K = 2 j2 (real) / 2 j2 + 1 (imaginary).
     //    Work units c = (j1, half of j2), two per warp; all values are read
     //    before any operand is written over them.
     {
@@ -294,20 +290,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int c = gw + 16 * u, j1 = c & 15, h = c >> 4;
-        uint4 hr, lr, hm, lm;
-        split2_bf16(x[u][0].x, x[u][1].x, hr.x, lr.x);
-        split2_bf16(x[u][2].x, x[u][3].x, hr.y, lr.y);
-        split2_bf16(x[u][4].x, x[u][5].x, hr.z, lr.z);
-        split2_bf16(x[u][6].x, x[u][7].x, hr.w, lr.w);
-        split2_bf16(x[u][0].y, x[u][1].y, hm.x, lm.x);
-        split2_bf16(x[u][2].y, x[u][3].y, hm.y, lm.y);
-        split2_bf16(x[u][4].y, x[u][5].y, hm.z, lm.z);
-        split2_bf16(x[u][6].y, x[u][7].y, hm.w, lm.w);
+        // j2 = 8h .. 8h + 3 fill K = 16h .. 16h + 7, j2 = 8h + 4 .. 8h + 7 the next 8
+        uint4 h0, l0, h1, l1;
+        split2_bf16(x[u][0].x, x[u][0].y, h0.x, l0.x);
+        split2_bf16(x[u][1].x, x[u][1].y, h0.y, l0.y);
+        split2_bf16(x[u][2].x, x[u][2].y, h0.z, l0.z);
+        split2_bf16(x[u][3].x, x[u][3].y, h0.w, l0.w);
+        split2_bf16(x[u][4].x, x[u][4].y, h1.x, l1.x);
+        split2_bf16(x[u][5].x, x[u][5].y, h1.y, l1.y);
+        split2_bf16(x[u][6].x, x[u][6].y, h1.z, l1.z);
+        split2_bf16(x[u][7].x, x[u][7].y, h1.w, l1.w);
         const int r = tc_row(j1, pl);
-        *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 8 * h)) = hr;
-        *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 8 * h)) = lr;
-        *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 16 + 8 * h)) = hm;
-        *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 16 + 8 * h)) = lm;
+        *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 16 * h)) = h0;
+        *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 16 * h)) = l0;
+        *reinterpret_cast<uint4*>(Ahi + tc_core_off(r, 16 * h + 8)) = h1;
+        *reinterpret_cast<uint4*>(Alo + tc_core_off(r, 16 * h + 8)) = l1;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -326,7 +323,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
     if (bad1) break;
 
     // 2. twiddle w256^(j1 k2) and re-layout as the stage-2 operand: row (pixel, k2),
-    //    K = j1 (real) / 16 + j1 (imaginary), over the stage-1 operand (its MMAs are done)
+    //    K = 2 j1 (real) / 2 j1 + 1 (imaginary), over the stage-1 operand (its MMAs are done)
     {
       float v[32];
       tc_ld32(tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(qblk * kTcK), v);
@@ -336,15 +333,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
       unsigned short* Alo = A + (kTcBlocks + qblk) * kABlock;
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
-        const float2 z = cmul(make_float2(v[k2], v[16 + k2]), tw[k2 * 16 + j1]);
-        const int r2 = tc_row(k2, pl);
-        unsigned short hr, lr, hm, lm;
-        split_bf16(z.x, hr, lr);
-        split_bf16(z.y, hm, lm);
-        Ahi[tc_core_off(r2, j1)] = hr;
-        Alo[tc_core_off(r2, j1)] = lr;
-        Ahi[tc_core_off(r2, 16 + j1)] = hm;
-        Alo[tc_core_off(r2, 16 + j1)] = lm;
+        const float2 z = cmul(make_float2(v[2 * k2], v[2 * k2 + 1]), tw[k2 * 16 + j1]);
+        const int off = tc_core_off(tc_row(k2, pl), 2 * j1);
+        unsigned hi, lo;
+        split2_bf16(z.x, z.y, hi, lo);
+        *reinterpret_cast<unsigned*>(Ahi + off) = hi;
+        *reinterpret_cast<unsigned*>(Alo + off) = lo;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -414,8 +408,8 @@ size_t axial_tc_table_elems() { return 2 * kTcK * kTcK; }
 
 // BF16 hi / lo of the real form of the 16-point DFT matrix (sign -), already in
 // the K-major core layout the kernel's B operand uses: B[n][k] with n = output
-// (k2 real for n < 16, k2 imaginary for n >= 16) and k = input (j2 real for
-// k < 16, j2 imaginary for k >= 16).
+// (2 k2: real part, 2 k2 + 1: imaginary part of output k2) and k = input
+// (2 j2: real part, 2 j2 + 1: imaginary part of input j2).
 void axial_tc_table(std::vector<unsigned short>& out) {
   out.assign(axial_tc_table_elems(), 0);
   const double pi = 3.14159265358979323846264338327950288;
@@ -433,12 +427,12 @@ void axial_tc_table(std::vector<unsigned short>& out) {
   };
   for (int n = 0; n < kTcK; ++n)
     for (int k = 0; k < kTcK; ++k) {
-      const int k2 = n % kTcR, j2 = k % kTcR;
+      const int k2 = n / 2, j2 = k / 2;
       const double a = -2.0 * pi * (double)((j2 * k2) % kTcR) / kTcR;
       const double c = std::cos(a), s = std::sin(a);
       double w;
-      if (n < kTcR) w = (k < kTcR) ? c : -s;   // Re Y = sum Hr c - Hi s
-      else w = (k < kTcR) ? s : c;             // Im Y = sum Hr s + Hi c
+      if (n % 2 == 0) w = (k % 2 == 0) ? c : -s;   // Re Y = sum Hr c - Hi s
+      else w = (k % 2 == 0) ? s : c;               // Im Y = sum Hr s + Hi c
       const unsigned short hi = bf16_bits((float)w);
       const unsigned short lo = bf16_bits((float)(w - (double)bf16_val(hi)));
       out[tc_core_off(n, k)] = hi;

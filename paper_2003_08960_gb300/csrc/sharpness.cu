@@ -39,8 +39,11 @@ struct Lat {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   static constexpr int NI = (N2 + N1 - 1) / N1;
   static constexpr int AS = NI * N1 > N2 ? NI * N1 : N2;
-  static constexpr int TW = kTile * N1 <= 512 ? kTile : kTile / 2;
 };
+// Column-tile width for axis length N (a variable template, instantiated only
+// for the column kernels that use it).
+template <int N>
+constexpr int kLatTW = kTile * Split<N>::N1 <= 512 ? kTile : kTile / 2;
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
@@ -152,8 +155,8 @@ __global__ void __launch_bounds__(kRowThreads) rows_fwd_kernel(const __grid_cons
 }
 
 template <int NY>
-__global__ void __launch_bounds__(Lat<NY>::TW * Lat<NY>::N1) cols_fwd_kernel(const __grid_constant__ ShParams p) {
-  constexpr int N1 = Lat<NY>::N1, N2 = Lat<NY>::N2, TW = Lat<NY>::TW;
+__global__ void __launch_bounds__(kLatTW<NY> * Lat<NY>::N1) cols_fwd_kernel(const __grid_constant__ ShParams p) {
+  constexpr int N1 = Lat<NY>::N1, N2 = Lat<NY>::N2, TW = kLatTW<NY>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int pix = threadIdx.x % TW, j1 = threadIdx.x / TW;
   const int x = blockIdx.x * TW + pix, t = blockIdx.y;
@@ -250,8 +253,8 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) axial_adj_kernel(const 
 }
 
 template <int NY>
-__global__ void __launch_bounds__(Lat<NY>::TW * Lat<NY>::N1) cols_adj_kernel(const __grid_constant__ ShParams p) {
-  constexpr int N1 = Lat<NY>::N1, N2 = Lat<NY>::N2, TW = Lat<NY>::TW;
+__global__ void __launch_bounds__(kLatTW<NY> * Lat<NY>::N1) cols_adj_kernel(const __grid_constant__ ShParams p) {
+  constexpr int N1 = Lat<NY>::N1, N2 = Lat<NY>::N2, TW = kLatTW<NY>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int pix = threadIdx.x % TW, j1 = threadIdx.x / TW;
   const int x = blockIdx.x * TW + pix, t = blockIdx.y;
@@ -421,7 +424,7 @@ cudaError_t rows(bool adjoint, const ShParams& p, int chunks, cudaStream_t s) {
 
 template <int NY>
 cudaError_t cols(bool adjoint, const ShParams& p, cudaStream_t s) {
-  constexpr int TW = Lat<NY>::TW;
+  constexpr int TW = kLatTW<NY>;
   const size_t smem = (size_t)Lat<NY>::N2 * Lat<NY>::N1 * TW * sizeof(float2);
   const dim3 grid(p.nx / TW, p.nl);
   if (adjoint) return launch_k(cols_adj_kernel<NY>, grid, TW * Lat<NY>::N1, smem, s, p);
