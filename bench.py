@@ -223,9 +223,15 @@ def run_ssoct(args):
     # schedule of the persistent lateral kernel (and axial form, if --tc-axial
     # is not forcing it) chosen by the library's autotuner on these frames
     tune = None
+    tune_cache = None
     if not args.no_autotune and not args.tc_axial:
-        tune = plan.autotune(frames, None, stream)
+        import tempfile
+        fd, tune_cache = tempfile.mkstemp(suffix=".json", prefix="ssoct_tune_")
+        os.close(fd)
+        os.unlink(tune_cache)  # the tuner writes it; other plans of the bench read the choice back
+        tune = plan.autotune(frames, tune_cache, stream)
     tc_main = args.tc_axial or bool(tune and tune["tc_axial"])
+    af_main = args.axial_first or bool(tune and tune["axial_first"])
     xy = torch.empty((wy, wx), dtype=torch.float32, device="cuda")
     xz = torch.empty((nl, wx), dtype=torch.float32, device="cuda")
     yz = torch.empty((nl, wy), dtype=torch.float32, device="cuda")
@@ -290,7 +296,8 @@ def run_ssoct(args):
     # end to end: pinned host frames -> ring (H2D) -> reconstruct -> volume to
     # pinned host (D2H); first of the extra lines, before the others fill the
     # device with their plans and graphs
-    e2e = _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world) if not args.no_e2e else None
+    e2e = (_e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world, flags, frames, tune_cache)
+           if not args.no_e2e else None)
     tc = _tc_form(args, ss, torch, w, frames, vol, stream, voxels, peak) if extra and not tc_main else None
     sliding = _sliding(args, ss, torch, plan, frames, vol, nl, voxels, stream) if extra else None
     if sliding is not None and args.size is None:
@@ -317,7 +324,7 @@ def run_ssoct(args):
         del ref
     if tc_plan is not None:
         del tc_plan
-    if args.axial_first:
+    if af_main:
         # rescale-axial pass: uint16 frames in, half-spectrum planes out; lateral
         # pass: the planes in (each read once from HBM, its conjugate use from L2),
         # |V|^2 out
@@ -336,7 +343,7 @@ def run_ssoct(args):
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     # the stored counters belong to the paper-order kernels at the 1024x1024x256 workload
     traffic = (_traffic("axial_tc" if (tc_main and dom == "axial") else dom)
-               if not args.axial_first and args.size is None else None)
+               if not af_main and args.size is None else None)
     whole_bytes = lat_bytes + ax_bytes
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -347,9 +354,9 @@ def run_ssoct(args):
         "config": {"workload": f"{w.nx}x{w.ny}x{nl} sweep, uint16 frames resident in HBM, full window, "
                                "|V|^2 volume + 3 cuts per step",
                    "window": [0, 0, wx, wy],
-                   "schedule": ({k: tune[k] for k in ("lag", "ring_slots", "tc_axial")} if tune
+                   "schedule": ({k: tune[k] for k in ("lag", "ring_slots", "tc_axial", "axial_first")} if tune
                                 else "plan default (lag 2, 6 ring slots)"),
-                   "form": ("fp32, axial-first order (Eq. 5 + Eq. 7, then Eq. 6 per depth bin)" if args.axial_first
+                   "form": ("fp32, axial-first order (Eq. 5 + Eq. 7, then Eq. 6 per depth bin)" if af_main
                             else "tensor-core axial (bf16 hi+lo, fp32 accumulate)" if tc_main else "fp32 (paper order)"),
                    "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["GBps"], "peak": peak,
@@ -378,13 +385,15 @@ def run_ssoct(args):
         out["cpu_baseline"]["single_core"] = {
             "value": r1 / 1e9, "unit": UNIT, "cores": 1,
             "sample": f"the same oracle with scipy.fft on one thread, first {n1} frames, {dt1:.1f} s"}
+    if tune_cache and os.path.exists(tune_cache):
+        os.unlink(tune_cache)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world):
+def _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world, flags, frames, tune_cache):
     """Same metric through the C ABI with host buffers: every step pushes its
     frames from pinned host memory into a plan's ring (H2D), reconstructs the
     volume and reads it back to pinned host memory (D2H), all inside the timed
@@ -397,7 +406,9 @@ def _e2e(args, ss, torch, dist, w, plan, vol, nl, voxels, world):
     on two streams, so the record shows whether the two directions overlap.
     The loop runs twice, with the D2H as one copy and as four chunks (one
     cudaMemcpyAsync each), and the line keeps the faster."""
-    plans = [plan, ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas)]
+    plans = [plan, ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas, flags=flags)]
+    if tune_cache:
+        plans[1].autotune(frames, tune_cache)  # the same choice as the main plan, from the cache
     vols = [vol, torch.empty_like(vol)]
     host_frames = torch.from_numpy(w.frames.view(np.int16)).pin_memory()
     host_vols = [torch.empty(vol.shape, dtype=torch.float32).pin_memory() for _ in range(2)]

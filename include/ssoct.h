@@ -295,13 +295,21 @@ typedef struct {
   double ms;       /* measured time of one reconstruction with this choice */
   int from_cache;  /* 1: read from the cache file, nothing timed */
   int candidates;  /* choices timed */
+  int axial_first; /* 1: whole-volume reconstructions run the axial-first order (SSOCT_FLAG_AXIAL_FIRST's) */
 } ssoct_tune_t;
 
 /* Time the plan's candidate schedules on frames_dev (reconstructing into the
  * scratch volume vol_dev, [nlambda][wy][wx] float) and keep the fastest: the
  * lateral kernel's (lag, ring slots) with lag 1..3 and lag + 2 <= slots <= the
  * workspace's slots, times the FP32 and tensor-core axial forms when nlambda is
- * 256.  With cache_path (NULL = none), a JSON file holding one entry per line
+ * 256, in the paper's order and, where the plan offers it, in the axial-first
+ * order (Eq. 5 + Eq. 7 before Eq. 6, the same V; offered when the frame size
+ * has the persistent lateral kernel, nlambda is 64, 128 or 256, the plan has no
+ * SSOCT_FLAG_PUPIL, and the half-spectrum planes fit in the sweep-axis
+ * intermediate, which that order does not use).  A plan made with
+ * SSOCT_FLAG_AXIAL_FIRST keeps that order.  An axial-first choice applies to
+ * whole-volume reconstructions only: sliding gates and
+ * ssoct_reconstruct_frames_noalloc keep the paper's order.  With cache_path (NULL = none), a JSON file holding one entry per line
  * keyed by GPU name, SM count, frame size, sweep length and window is read
  * first (a hit applies the stored choice without timing) and updated after
  * timing.  The choice stays with the plan; results are the same up to the

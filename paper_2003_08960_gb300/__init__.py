@@ -309,7 +309,7 @@ class Plan:
 
 
 def ssoct_autotune(plan, frames_ptr: int, vol_ptr: int, cache_path, stream: int):
-    """Returns (status, dict with lag, ring_slots, tc_axial, ms, from_cache, candidates)."""
+    """Returns (status, dict with lag, ring_slots, tc_axial, ms, from_cache, candidates, axial_first)."""
     r = _abi.ssoct_tune_t()
     path = None if cache_path is None else str(cache_path).encode()
     st = _abi.lib().ssoct_autotune(plan, C.c_void_p(frames_ptr), C.c_void_p(vol_ptr), path, C.c_void_p(stream),

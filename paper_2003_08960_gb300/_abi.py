@@ -53,7 +53,7 @@ class ssoct_plan_info_t(C.Structure):
 
 class ssoct_tune_t(C.Structure):
     _fields_ = [("lag", C.c_int), ("ring_slots", C.c_int), ("tc_axial", C.c_int), ("ms", C.c_double),
-                ("from_cache", C.c_int), ("candidates", C.c_int)]
+                ("from_cache", C.c_int), ("candidates", C.c_int), ("axial_first", C.c_int)]
 
 
 ssoct_plan = C.c_void_p

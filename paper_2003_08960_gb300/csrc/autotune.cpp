@@ -1,7 +1,9 @@
-// Autotuner: picks, per plan and GPU, the schedule of the persistent lateral
-// kernel (lag between a frame's row and column items, number of L2 scratch-ring
-// slots) and the form of the axial pass (FP32 or tensor cores, 256-frame
-// sweeps), by timing whole reconstructions on the caller's frames.  Choices are
+// Autotuner: picks, per plan and GPU, the order of the steps (the paper's, or
+// the axial-first order where the plan offers it), the schedule of the
+// persistent lateral kernel (lag between a frame's row and column items,
+// number of L2 scratch-ring slots) and the form of the axial pass (FP32 or
+// tensor cores, 256-frame sweeps, paper order), by timing whole
+// reconstructions on the caller's frames.  Choices are
 // cached in a small JSON file, one entry per line, keyed by GPU name, SM count,
 // frame size, sweep length and window.
 #include <cstdio>
@@ -17,7 +19,7 @@ using namespace ssoct;
 namespace {
 
 struct Choice {
-  int lag, slots, tc;
+  int lag, slots, tc, af;
 };
 
 std::string tune_key(const Plan& p) {
@@ -28,7 +30,7 @@ std::string tune_key(const Plan& p) {
     if (c == '"' || c == '\\') c = '_';
   char buf[256];
   snprintf(buf, sizeof buf, "%s|%d|%dx%dx%d|%d,%d,%d,%d%s", name.c_str(), p.num_sms, p.nx, p.ny, p.nl, p.x0, p.y0,
-           p.wx, p.wy, p.axial_first ? "|axial-first" : "");
+           p.wx, p.wy, p.af_forced ? "|axial-first" : "");
   return buf;
 }
 
@@ -50,8 +52,8 @@ bool find_entry(const std::vector<std::string>& entries, const std::string& key,
   for (const std::string& e : entries) {
     const size_t at = e.find(tag);
     if (at == std::string::npos) continue;
-    if (sscanf(e.c_str() + at + tag.size(), ", \"lag\": %d, \"slots\": %d, \"tc_axial\": %d, \"ms\": %lf", &c.lag,
-               &c.slots, &c.tc, &ms) == 4)
+    if (sscanf(e.c_str() + at + tag.size(), ", \"lag\": %d, \"slots\": %d, \"tc_axial\": %d, \"axial_first\": %d, \"ms\": %lf",
+               &c.lag, &c.slots, &c.tc, &c.af, &ms) == 5)
       return true;
   }
   return false;
@@ -61,8 +63,8 @@ bool write_entries(const char* path, std::vector<std::string> entries, const std
                    double ms) {
   const std::string tag = "\"key\": \"" + key + "\"";
   char buf[512];
-  snprintf(buf, sizeof buf, "{%s, \"lag\": %d, \"slots\": %d, \"tc_axial\": %d, \"ms\": %.6f}", tag.c_str(), c.lag,
-           c.slots, c.tc, ms);
+  snprintf(buf, sizeof buf, "{%s, \"lag\": %d, \"slots\": %d, \"tc_axial\": %d, \"axial_first\": %d, \"ms\": %.6f}",
+           tag.c_str(), c.lag, c.slots, c.tc, c.af, ms);
   bool replaced = false;
   for (std::string& e : entries)
     if (e.find(tag) != std::string::npos) {
@@ -82,6 +84,8 @@ bool valid(const Plan& p, const Choice& c) {
   if (c.lag < 1 || c.lag > p.nl - 1) return false;
   if (c.slots < c.lag + 2 || c.slots > p.slots_alloc) return false;
   if (c.tc && !axial_tc_supported(p.nl)) return false;
+  if (c.af ? !(p.af_forced || p.af_option) : p.af_forced) return false;
+  if (c.af && c.tc) return false;  // the tensor-core form is the paper order's axial pass
   return true;
 }
 
@@ -89,6 +93,7 @@ void apply(Plan& p, const Choice& c) {
   p.sch.lag = c.lag;
   p.sch.slots = c.slots;
   p.use_tc = c.tc != 0;
+  p.axial_first = c.af != 0;
   p.lat_upto = -1;  // slot numbering of the sliding-gate state changes with the ring
 }
 
@@ -103,8 +108,8 @@ extern "C" ssoct_status ssoct_autotune(ssoct_plan h, const uint16_t* frames_dev,
   if (p.profiling || p.inject_skip) return SSOCT_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const std::string key = tune_key(p);
-  const Choice initial{p.sch.lag, p.sch.slots, p.use_tc ? 1 : 0};
-  *result = ssoct_tune_t{initial.lag, initial.slots, initial.tc, 0.0, 0, 0};
+  const Choice initial{p.sch.lag, p.sch.slots, p.use_tc ? 1 : 0, p.axial_first ? 1 : 0};
+  *result = ssoct_tune_t{initial.lag, initial.slots, initial.tc, 0.0, 0, 0, initial.af};
 
   std::vector<std::string> entries;
   if (cache_path) {
@@ -113,26 +118,29 @@ extern "C" ssoct_status ssoct_autotune(ssoct_plan h, const uint16_t* frames_dev,
     double ms = 0.0;
     if (find_entry(entries, key, c, ms) && valid(p, c)) {
       apply(p, c);
-      *result = ssoct_tune_t{c.lag, c.slots, c.tc, ms, 1, 0};
+      *result = ssoct_tune_t{c.lag, c.slots, c.tc, ms, 1, 0, c.af};
       return SSOCT_OK;
     }
   }
 
-  // Candidates: the persistent kernel's schedule (generic-path plans have none)
-  // times the axial forms this sweep length has.
+  // Candidates: the orders the plan offers, times the persistent kernel's
+  // schedule (generic-path plans have none), times the axial forms this sweep
+  // length has (paper order).
   std::vector<Choice> cand;
   const int lags[] = {1, 2, 3};
-  for (int tc = 0; tc <= (axial_tc_supported(p.nl) && !p.axial_first ? 1 : 0); ++tc) {
-    if (p.generic) {
-      cand.push_back(Choice{initial.lag, initial.slots, tc});
-      continue;
-    }
-    for (int lag : lags)
-      for (int slots = lag + 2; slots <= p.slots_alloc; ++slots) {
-        const Choice c{lag, slots, tc};
+  for (int af = 0; af <= 1; ++af)
+    for (int tc = 0; tc <= 1; ++tc) {
+      if (p.generic) {
+        const Choice c{initial.lag, initial.slots, tc, af};
         if (valid(p, c)) cand.push_back(c);
+        continue;
       }
-  }
+      for (int lag : lags)
+        for (int slots = lag + 2; slots <= p.slots_alloc; ++slots) {
+          const Choice c{lag, slots, tc, af};
+          if (valid(p, c)) cand.push_back(c);
+        }
+    }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return SSOCT_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -165,7 +173,7 @@ extern "C" ssoct_status ssoct_autotune(ssoct_plan h, const uint16_t* frames_dev,
     return st;
   }
   apply(p, best);
-  *result = ssoct_tune_t{best.lag, best.slots, best.tc, best_ms, 0, (int)cand.size()};
+  *result = ssoct_tune_t{best.lag, best.slots, best.tc, best_ms, 0, (int)cand.size(), best.af};
   if (cache_path && !write_entries(cache_path, entries, key, best, best_ms)) {
     p.last_error = std::string("could not write the tuning cache ") + cache_path;
     return SSOCT_EINVAL;

@@ -80,7 +80,8 @@ extern "C" ssoct_status ssoct_reconstruct_frames_noalloc(ssoct_plan h, const uin
                                                          void* complex_dev, void* stream) {
   if (!h) return SSOCT_EINVAL;
   Plan& p = plan_of(h);
-  if (p.axial_first) return fail(p, SSOCT_EUNSUPPORTED, "the no-allocation entry point runs the paper's order");
+  if (p.af_forced) return fail(p, SSOCT_EUNSUPPORTED, "the no-allocation entry point runs the paper's order");
+  PaperOrderScope paper_order(p);  // an autotuned axial-first choice does not apply here
   if (p.generic) return fail(p, SSOCT_EUNSUPPORTED, "the no-allocation entry point needs a frame size of the persistent lateral kernel");
   if (p.ws_bytes > kNoAllocBytes) {
     char msg[200];

@@ -203,7 +203,9 @@ struct Plan {
   size_t off_cg = 0;
   // SSOCT_FLAG_AXIAL_FIRST: Eq. 5 + Eq. 7 first (half spectrum of the real
   // rescaled frames), then the lateral kernel on the planes
-  bool axial_first = false;
+  bool axial_first = false;  // order of whole-volume reconstructions (the flag's, or the autotuner's choice)
+  bool af_forced = false;    // created with SSOCT_FLAG_AXIAL_FIRST: every call runs that order
+  bool af_option = false;    // the autotuner may pick the axial-first order (its planes fit the intermediate)
   size_t off_aplanes = 0;
   // tiled first pass (rescale_axial_tiled): strip records [nl][nx / 64] and the
   // staged columns per source row (0: the one-tile-per-CTA kernel instead)
@@ -303,6 +305,18 @@ cudaError_t launch_axial_with(const Plan& p, const AxialParams& ap, int num_sms,
 // Error word of the last no-allocation call made with this plan (0 if none, or
 // if that call's kernels met no time-out); read after the caller's stream sync.
 cudaError_t noalloc_error_word(Plan& p, unsigned* err);
+// Runs the paper's order for one call on a plan whose axial-first order was
+// only the autotuner's choice (sliding gates and the no-allocation path keep
+// the paper's order); restores the plan's order when it goes out of scope.
+struct PaperOrderScope {
+  Plan& p;
+  bool saved;
+  explicit PaperOrderScope(Plan& pl) : p(pl), saved(pl.axial_first) {
+    if (!p.af_forced) p.axial_first = false;
+  }
+  ~PaperOrderScope() { p.axial_first = saved; }
+};
+
 // Whole-frame window: the lateral kernel then needs no window bounds checks.
 inline bool lateral_full_window(const Plan& p) { return p.x0 == 0 && p.y0 == 0 && p.wx == p.nx && p.wy == p.ny; }
 

@@ -214,7 +214,8 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.x0 = w.x0; p.y0 = w.y0; p.wx = w.wx; p.wy = w.wy;
   p.flags = flags;
   p.generic = generic;
-  p.axial_first = (flags & SSOCT_FLAG_AXIAL_FIRST) != 0;
+  p.af_forced = (flags & SSOCT_FLAG_AXIAL_FIRST) != 0;
+  p.axial_first = p.af_forced;
   p.pitch = pitch_m; p.z = z_m;
   p.lambdas.assign(lambda_m, lambda_m + nlambda);
   p.lambda1 = lambda_m[0];
@@ -240,7 +241,9 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   // Axial-first order, tiled first pass: one strip record per (frame, 64-pixel
   // strip), and the staged width that holds every frame's taps of a strip
   // (one column of slack at each end for the float32 position's rounding).
-  if (p.axial_first && !generic && rescale_axial_tiled(nx, nlambda)) {
+  // Built for every plan whose sizes the tiled pass takes: the autotuner may
+  // choose that order for plans created without the flag.
+  if (!generic && rescale_axial_tiled(nx, nlambda)) {
     const int strips = nx / 64;
     p.xstrip.resize((size_t)nlambda * strips);
     int wmax = 0;
@@ -343,11 +346,19 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_wq = take(sizeof(float2) * p.wq.size());
   p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
   p.off_scratch = take(generic ? 0 : sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
-  p.off_inter = take(sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile);
+  const size_t inter_bytes = sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile;
+  p.off_inter = take(inter_bytes);
   if (generic) p.off_cg = take(sizeof(float2) * (size_t)nx * ny);
-  if (p.axial_first) p.off_aplanes = take(sizeof(float2) * (size_t)(nlambda / 2 + 1) * ny * nx);
+  // The axial-first order never uses the sweep-axis intermediate, so its
+  // half-spectrum planes share that region when they fit in it.
+  const size_t planes_bytes = sizeof(float2) * (size_t)(nlambda / 2 + 1) * ny * nx;
+  if (p.af_forced) p.off_aplanes = planes_bytes <= inter_bytes ? p.off_inter : take(planes_bytes);
+  else if (!generic && p.ra_w && planes_bytes <= inter_bytes && !(flags & SSOCT_FLAG_PUPIL)) {
+    p.off_aplanes = p.off_inter;
+    p.af_option = true;
+  }
   if (p.ra_w) p.off_xstrip = take(sizeof(StripTap) * p.xstrip.size());
-  if (!generic && !p.axial_first) p.off_xys = take(sizeof(float2) * (size_t)p.wy * p.ntx * kTile);
+  if (!generic && !p.af_forced) p.off_xys = take(sizeof(float2) * (size_t)p.wy * p.ntx * kTile);
   if (generic || (flags & SSOCT_FLAG_PUPIL)) p.off_F = take(sizeof(float2) * (size_t)nlambda * ny * nx);
   if (flags & SSOCT_FLAG_PUPIL) {
     const size_t chunks = (size_t)(nlambda + p.sh_tpc - 1) / p.sh_tpc;
@@ -622,7 +633,7 @@ ssoct_status ssoct_reconstruct_frames(ssoct_plan h, const uint16_t* frames_dev, 
 static ssoct_status sliding_update(Plan& p, cudaStream_t s, cudaEvent_t** ev_out) {
   if (!p.ws) return fail(&p, SSOCT_ENOMEM, "no workspace");
   if (p.generic) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need a frame size of the persistent lateral kernel");
-  if (p.axial_first) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need the paper's order (no SSOCT_FLAG_AXIAL_FIRST)");
+  if (p.af_forced) return fail(&p, SSOCT_EUNSUPPORTED, "sliding gates need the paper's order (no SSOCT_FLAG_AXIAL_FIRST)");
   if (p.stream_count < p.nl) return fail(&p, SSOCT_ENOTREADY, "fewer than nlambda frames pushed");
   // holograms still missing for the gate of the last nl frames: stream frames
   // [first, stream_count), in ring slots first % nl onwards
@@ -664,6 +675,7 @@ ssoct_status ssoct_reconstruct_sliding(ssoct_plan h, float* vol_dev, void* compl
   if (!vol_dev || ((uintptr_t)vol_dev % 16) || ((uintptr_t)complex_dev % 16))
     return fail(&p, SSOCT_EINVAL, "volume pointer NULL or not 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
+  PaperOrderScope paper_order(p);
   cudaEvent_t* ev = nullptr;
   ssoct_status st = sliding_update(p, s, &ev);
   if (st != SSOCT_OK) return st;
@@ -676,6 +688,7 @@ ssoct_status ssoct_sliding_cuts(ssoct_plan h, int x0, int y0, int z0, float* xy,
   if (x0 < 0 || x0 >= p.wx || y0 < 0 || y0 >= p.wy || z0 < 0 || z0 >= p.nl)
     return fail(&p, SSOCT_EINVAL, "cut position outside the volume");
   cudaStream_t s = (cudaStream_t)stream;
+  PaperOrderScope paper_order(p);
   // The xy cut is kept as a running sum X(z0) over the gate's slots while z0
   // stays put: the frames this call swaps in change it by their holograms minus
   // those they replace.  Once nl frames have been swapped in since the last
