@@ -341,9 +341,13 @@ def run_ssoct(args):
     for k in kernels.values():
         k["frac"] = k["GBps"] / peak
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    # the stored counters belong to the paper-order kernels at the 1024x1024x256 workload
-    traffic = (_traffic("axial_tc" if (tc_main and dom == "axial") else dom)
-               if not af_main and args.size is None else None)
+    # stored counters of the kernel that dominates this line's form, taken at the
+    # 1024x1024x256 workload (see profiles/traffic.json)
+    if af_main:
+        tkey = {"lateral": "lateral_af", "axial": "rescale_axial"}[dom]
+    else:
+        tkey = "axial_tc" if (tc_main and dom == "axial") else dom
+    traffic = _traffic(tkey) if args.size is None else None
     whole_bytes = lat_bytes + ax_bytes
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(co
 // Same output as rescale_axial_kernel for sweeps of 64, 128 and 256 frames, with
 // the frames read once and the real input used twice over:
 //  * a tile is 64 consecutive pixels of one sensor row (a 64-pixel strip x one
-//    row); pixels p and p + 32 are paired into one complex series
+//    row), tiles numbered row by row, so that the CTAs running together cover
+//    neighbouring strips of neighbouring rows and share in L2 the source lines
+//    their staged boxes overlap on (numbered strip by strip, the frames were
+//    read 2.2 times from DRAM); pixels p and p + 32 are paired into one complex series
 //    z_t = u_t(p) + i u_t(p + 32), so 32 complex N_lambda-point DFTs give the
 //    64 real ones: X(p) = (Z_q + conj Z_{N-q}) / 2 and
 //    X(p + 32) = (Z_q - conj Z_{N-q}) / (2i);
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
   };
   auto records = [&](int tile, StripTap& xr, Tap& yr) {
     if (loader && tile < ntiles) {
-      const int strip = tile / p.ny, y = tile - strip * p.ny;
+      const int y = tile / strips, strip = tile - y * strips;
       xr = p.xstrip[(size_t)tid * strips + strip];
       yr = p.ytab[(size_t)tid * p.ny + y];
     }
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
     if (__syncthreads_or(!ok)) break;
     pending = false;
     ++phase;
-    const int strip = tile / p.ny, y = tile - strip * p.ny;
+    const int y = tile / strips, strip = tile - y * strips;
     // 1. Eq. 5 samples of frames t = j1 + N1 j2 at pixels pp and pp + 32 (one
     //    complex series), N2-point DFT over j2, twiddle, exchange
     float2 a[N2];
