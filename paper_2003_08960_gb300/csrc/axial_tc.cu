@@ -18,18 +18,19 @@
 // scaling is needed), and D = Ahi Bhi + Ahi Blo + Alo Bhi; the dropped Alo Blo
 // term and the rounding of lo put the relative error near 2^-16 per stage.
 //
-// The kernel is persistent, one CTA per SM, fed like the FP32 streaming axial
-// kernel: whole tiles (256 x 32 complex values, contiguous in the sweep-axis
-// intermediate) arrive by 1D TMA bulk copies into a ring of three 64 KB
-// shared-memory buffers, a ring's worth ahead, and two groups of 16 warps
-// compute the CTA's tiles g, g + 2, ...  A tile never leaves its buffer: the
-// FP32 values are read into registers and written back as the BF16 hi / lo
-// stage-1 operands (the same 64 KB), the stage-2 operands overwrite those once
-// the stage-1 MMAs are done, and the |V|^2 rows overwrite those once the
-// stage-2 MMAs are done.  Each group owns 128 TMEM columns (4 blocks x N = 32
-// fp32 accumulators), one thread issues its 24 MMAs per stage and waits on its
-// commit barrier, and while one group waits for its MMAs or its next tile the
-// other computes.
+// The kernel is persistent, one CTA per SM.  Its unit of work is half a tile:
+// 16 pixels x 256 frames (two 8-pixel M blocks), which a 2D tensor copy (TMA)
+// takes out of the 32-pixel tile of the sweep-axis intermediate into a ring of
+// six 32 KB shared-memory buffers, a ring's worth ahead.  Four groups of 8
+// warps compute the CTA's half-tiles g, g + 4, ...; while one group waits for
+// its MMAs or its next half-tile, three others compute.  (Two groups on whole
+// 64 KB tiles spent 43 % of their stall samples at barriers and took 0.73 ms.)
+// A half-tile never leaves its buffer: the FP32 values are read into registers
+// and written back as the BF16 hi / lo stage-1 operands (the same 32 KB), the
+// stage-2 operands overwrite those once the stage-1 MMAs are done, and the
+// |V|^2 rows overwrite those once the stage-2 MMAs are done.  Each group owns
+// 64 TMEM columns (2 blocks x N = 32 fp32 accumulators); one of its threads
+// issues its 12 MMAs per stage and waits on its commit barrier.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -44,15 +45,16 @@ namespace {
 
 constexpr int kTcN = 256;          // sweep length this kernel is built for
 constexpr int kTcR = 16;           // radix of both stages
-constexpr int kTcBlocks = 4;       // 8-pixel M blocks per 32-pixel tile
 constexpr int kTcK = 2 * kTcR;     // 32: real + imaginary parts
-constexpr int kTcGroups = 2;       // tiles computed at once per CTA
-constexpr int kTcGroupThreads = 512;
+constexpr int kTcGroups = 4;       // half-tiles computed at once per CTA
+constexpr int kTcGroupThreads = 256;
 constexpr int kTcThreads = kTcGroups * kTcGroupThreads;
-constexpr unsigned kTcCols = kTcBlocks * kTcK;  // TMEM columns (fp32 accumulators) per group
-constexpr int kTcStages = 3;                    // ring buffers
-constexpr int kTcFull = 6;                      // full barriers: tile mod lcm(stages, groups)
-constexpr size_t kTcTileBytes = (size_t)kTcN * kTile * sizeof(float2);  // 64 KB
+constexpr int kTcHalf = 16;                     // pixels per work item (half a 32-pixel tile)
+constexpr int kTcItemBlocks = kTcHalf / 8;      // 8-pixel M blocks per work item
+constexpr unsigned kTcCols = kTcItemBlocks * kTcK;  // TMEM columns (fp32 accumulators) per group
+constexpr int kTcStages = 6;                    // ring buffers
+constexpr int kTcFull = 12;                     // full barriers: item mod lcm(stages, groups)
+constexpr size_t kTcItemBytes = (size_t)kTcN * kTcHalf * sizeof(float2);  // 32 KB
 constexpr unsigned long long kTcLoadWaitNs = 4000000000ull;
 constexpr unsigned long long kTcWaitNs = 1000000000ull;
 
@@ -150,7 +152,7 @@ __device__ __forceinline__ void split2_bf16(float a, float b, unsigned& hi, unsi
 // i * 8 + pl keeps a warp's 32 pixels on distinct 16-byte slots of a core matrix.
 __device__ __forceinline__ int tc_row(int i, int pl) { return i * 8 + pl; }
 
-// Barrier of one group (named barrier 1 + g, 512 threads); returns the OR of v.
+// Barrier of one group (named barrier 1 + g, 256 threads); returns the OR of v.
 __device__ __forceinline__ bool tc_group_sync_or(int g, bool v) {
   unsigned r;
   asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
@@ -163,26 +165,36 @@ __device__ __forceinline__ void tc_group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kTcGroupThreads) : "memory");
 }
 
-constexpr int kABlock = 128 * kTcK;  // elements of one M block of an operand
-constexpr int kOutStride = 40;       // floats per |V|^2 row in the buffer; conflict-free both ways
-
-// Copy of the CTA's tile t (global tile blockIdx.x + t * gridDim.x) into ring buffer t mod kTcStages.
-__device__ __forceinline__ void tc_fill(const TcParams& p, unsigned char* ring, uint64_t* full, unsigned* fills, int t) {
-  const int f = t % kTcFull;
-  ++fills[f];
-  mbar_arrive_tx(&full[f], (unsigned)kTcTileBytes);
-  const size_t gt = blockIdx.x + (size_t)t * gridDim.x;
-  tma_load_1d(ring + (size_t)(t % kTcStages) * kTcTileBytes, p.inter + gt * kTcN * kTile, (unsigned)kTcTileBytes,
-              &full[f]);
+__device__ __forceinline__ void tc_tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
 }
 
-// 24 MMAs of one stage: D[blk] = Ahi Bhi + Ahi Blo + Alo Bhi, K = 32 as two K = 16 steps.
+constexpr int kABlock = 128 * kTcK;  // elements of one M block of an operand
+constexpr int kOutStride = 24;       // floats per |V|^2 row in the buffer: conflict-free writes
+
+// Copy of the CTA's work item t (global item blockIdx.x + t * gridDim.x: half
+// item % 2 of tile item / 2) into ring buffer t mod kTcStages.  The tensor map
+// sees the intermediate as float [tiles * 256][64]; a box is 32 floats (16
+// complex values) x 256 rows.
+__device__ __forceinline__ void tc_fill(const CUtensorMap* map, unsigned char* ring, uint64_t* full, unsigned* fills,
+                                        int t) {
+  const int f = t % kTcFull;
+  atomicAdd(&fills[f], 1u);
+  mbar_arrive_tx(&full[f], (unsigned)kTcItemBytes);
+  const int gi = (int)blockIdx.x + t * (int)gridDim.x;
+  tc_tma_2d(ring + (size_t)(t % kTcStages) * kTcItemBytes, map, (gi & 1) * 2 * kTcHalf, (gi >> 1) * kTcN, &full[f]);
+}
+
+// 12 MMAs of one stage: D[blk] = Ahi Bhi + Ahi Blo + Alo Bhi, K = 32 as two K = 16 steps.
 __device__ __forceinline__ void tc_issue_stage(unsigned tmem, const unsigned short* A, const unsigned short* Bs,
                                                uint64_t* bar) {
   const unsigned idesc = tc_idesc(128, kTcK);
 #pragma unroll 1
-  for (int blk = 0; blk < kTcBlocks; ++blk) {
-    const unsigned short* a_terms[3] = {A + blk * kABlock, A + blk * kABlock, A + (kTcBlocks + blk) * kABlock};
+  for (int blk = 0; blk < kTcItemBlocks; ++blk) {
+    const unsigned short* a_terms[3] = {A + blk * kABlock, A + blk * kABlock, A + (kTcItemBlocks + blk) * kABlock};
     const unsigned short* b_terms[3] = {Bs, Bs + kTcK * kTcK, Bs};
     bool acc = false;
 #pragma unroll
@@ -198,7 +210,7 @@ __device__ __forceinline__ void tc_issue_stage(unsigned tmem, const unsigned sho
 }
 
 // |V|^2 |K|^2 (|V| |K| if MAG) of the 16 depth bins q = k2 + 16 k1 this thread
-// holds into the tile's output rows; with CPLX also V with the output chirp and K.
+// holds into the item's output rows; with CPLX also V with the output chirp and K.
 template <bool MAG, bool CPLX>
 __device__ __forceinline__ void tc_epilogue(const TcParams& p, const float (&v)[32], float* out, int k2, int px,
                                             int kx0, int kyw) {
@@ -220,18 +232,19 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, const float (&v)[
   }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(kTcThreads, 1)
+    axial_tc_kernel(const __grid_constant__ TcParams p, const __grid_constant__ CUtensorMap imap) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* ring = smem;                                                      // [3][64 KB]
-  unsigned short* Bs = reinterpret_cast<unsigned short*>(ring + kTcStages * kTcTileBytes);  // [hi / lo][32 x 32]
+  unsigned char* ring = smem;                                                      // [6][32 KB]
+  unsigned short* Bs = reinterpret_cast<unsigned short*>(ring + kTcStages * kTcItemBytes);  // [hi / lo][32 x 32]
   float2* tw = reinterpret_cast<float2*>(Bs + 2 * kTcK * kTcK);                    // [256]
   __shared__ __align__(8) uint64_t full[kTcFull];
   __shared__ __align__(8) uint64_t mma_bar[kTcGroups];
   __shared__ unsigned fills[kTcFull];
   __shared__ unsigned tmem_base;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int ntiles = p.ntx * p.wy;
-  const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nitems = 2 * p.ntx * p.wy;
+  const int mine = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
@@ -246,7 +259,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
     }
     for (int g = 0; g < kTcGroups; ++g) mbar_init(&mma_bar[g], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int t = 0; t < kTcStages && t < mine; ++t) tc_fill(p, ring, full, fills, t);
+    for (int t = 0; t < kTcStages && t < mine; ++t) tc_fill(&imap, ring, full, fills, t);
   }
   if (tid < 256) reinterpret_cast<uint4*>(Bs)[tid] = __ldg(reinterpret_cast<const uint4*>(p.bmat) + tid);  // 4 KB
   if (tid < kTcN) tw[tid] = ldg2(p.twl + tid);
@@ -255,41 +268,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
   tc_fence_after();
   const int g = tid / kTcGroupThreads;
   const int lt = tid % kTcGroupThreads;
-  const int gw = lt / 32;                       // warp within the group (0..15)
+  const int gw = lt / 32;                       // warp within the group (0..7)
   const int quad = gw & 3, qblk = gw >> 2;      // TMEM lane quadrant, M block read by this warp
   const unsigned tmem = tmem_base + (unsigned)(g * kTcCols);
   for (int i = g, prev = -1;; prev = i, i += kTcGroups) {
-    tc_group_sync(g);  // every thread of the group is done with tile prev's buffer
-    if (lt == 0 && prev >= 0 && prev + kTcStages < mine) tc_fill(p, ring, full, fills, prev + kTcStages);
+    tc_group_sync(g);  // every thread of the group is done with item prev's buffer
+    if (lt == 0 && prev >= 0 && prev + kTcStages < mine) tc_fill(&imap, ring, full, fills, prev + kTcStages);
     if (i >= mine) break;
     const bool ok0 = tc_wait(&full[i % kTcFull], (unsigned)(i / kTcFull) & 1u, kTcLoadWaitNs);
     if (!ok0 && lt == 0) atomicOr(p.err, kErrAxial);
     if (tc_group_sync_or(g, !ok0)) break;
-    unsigned char* buf = ring + (size_t)(i % kTcStages) * kTcTileBytes;
+    unsigned char* buf = ring + (size_t)(i % kTcStages) * kTcItemBytes;
     unsigned short* A = reinterpret_cast<unsigned short*>(buf);  // [hi / lo][block][128 x 32]
-    const int gt = (int)blockIdx.x + i * (int)gridDim.x;
+    const int gi = (int)blockIdx.x + i * (int)gridDim.x;
+    const int gt = gi >> 1;
     const int kyw = gt / p.ntx;
-    const int kx0 = (gt - kyw * p.ntx) * kTile;
+    const int kx0 = (gt - kyw * p.ntx) * kTile + (gi & 1) * kTcHalf;
 
     // 1. t = j1 + 16 j2 -> stage-1 row (pixel, j1), K = 2 j2 (real) / 2 j2 + 1 (imaginary).
-    //    Work units c = (j1, half of j2), two per warp; all values are read
-    //    before any operand is written over them.
+    //    Work units c = (j1, half of j2): a warp takes four, a thread two
+    //    (lanes 0-15 and 16-31 on different units); every value is read before
+    //    any operand is written over it.
     {
-      const float2* src = reinterpret_cast<const float2*>(buf) + lane;
+      const int px = lane & (kTcHalf - 1), usel = lane >> 4;
+      const float2* src = reinterpret_cast<const float2*>(buf) + px;
       float2 x[2][8];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int c = gw + 16 * u, j1 = c & 15, h = c >> 4;
+        const int c = gw * 4 + u * 2 + usel, j1 = c & 15, h = c >> 4;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[u][k] = src[(j1 + 16 * (8 * h + k)) * kTile];
+        for (int k = 0; k < 8; ++k) x[u][k] = src[(j1 + 16 * (8 * h + k)) * kTcHalf];
       }
       tc_group_sync(g);
-      const int blk = lane >> 3, pl = lane & 7;
+      const int blk = px >> 3, pl = px & 7;
       unsigned short* Ahi = A + blk * kABlock;
-      unsigned short* Alo = A + (kTcBlocks + blk) * kABlock;
+      unsigned short* Alo = A + (kTcItemBlocks + blk) * kABlock;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int c = gw + 16 * u, j1 = c & 15, h = c >> 4;
+        const int c = gw * 4 + u * 2 + usel, j1 = c & 15, h = c >> 4;
         // j2 = 8h .. 8h + 3 fill K = 16h .. 16h + 7, j2 = 8h + 4 .. 8h + 7 the next 8
         uint4 h0, l0, h1, l1;
         split2_bf16(x[u][0].x, x[u][0].y, h0.x, l0.x);
@@ -330,7 +346,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
       const int r = quad * 32 + lane;
       const int j1 = r >> 3, pl = r & 7;
       unsigned short* Ahi = A + qblk * kABlock;
-      unsigned short* Alo = A + (kTcBlocks + qblk) * kABlock;
+      unsigned short* Alo = A + (kTcItemBlocks + qblk) * kABlock;
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
         const float2 z = cmul(make_float2(v[2 * k2], v[2 * k2 + 1]), tw[k2 * 16 + j1]);
@@ -355,7 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
     tc_fence_after();
     if (bad2) break;
 
-    // 3. V[k2 + 16 k1] sits in row (pixel, k2), columns k1 (real) / 16 + k1
+    // 3. V[k2 + 16 k1] sits in row (pixel, k2), columns 2 k1 (real) / 2 k1 + 1
     //    (imaginary); |V|^2 rows over the stage-2 operand (its MMAs are done)
     float* out = reinterpret_cast<float*>(buf);  // [256][kOutStride]
     {
@@ -372,12 +388,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
       }
     }
     tc_group_sync(g);
-    // 4. 128-byte rows of the volume
-    if (kx0 + lane < p.wx) {
-      float* dst = p.vol + (size_t)kyw * p.wx + kx0 + lane;
-      const size_t plane = (size_t)p.wy * p.wx;
+    // 4. 64-byte rows of the volume: per pass 16 depth bins, a warp's two halves
+    //    on bins two apart (distinct banks with the 24-float row stride)
+    {
+      const int px = lane & (kTcHalf - 1);
+      const int qa = (gw & 1) + 4 * (gw >> 1) + 2 * (lane >> 4);
+      if (kx0 + px < p.wx) {
+        float* dst = p.vol + (size_t)kyw * p.wx + kx0 + px;
+        const size_t plane = (size_t)p.wy * p.wx;
 #pragma unroll 4
-      for (int q = gw; q < kTcN; q += kTcGroupThreads / 32) __stcs(dst + (size_t)q * plane, out[q * kOutStride + lane]);
+        for (int q = qa; q < kTcN; q += 16) __stcs(dst + (size_t)q * plane, out[q * kOutStride + px]);
+      }
     }
     // this thread's accesses to the buffer come before its next TMA fill (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -401,7 +422,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) axial_tc_kernel(const __grid_co
 bool axial_tc_supported(int nl) { return nl == kTcN; }
 
 size_t axial_tc_smem_bytes() {
-  return (size_t)kTcStages * kTcTileBytes + (size_t)2 * kTcK * kTcK * 2 + kTcN * sizeof(float2);
+  return (size_t)kTcStages * kTcItemBytes + (size_t)2 * kTcK * kTcK * 2 + kTcN * sizeof(float2);
 }
 
 size_t axial_tc_table_elems() { return 2 * kTcK * kTcK; }
@@ -459,11 +480,13 @@ cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigne
   const size_t smem = axial_tc_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(axial_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long ntiles = (long long)ap.ntx * ap.wy;
+  alignas(64) CUtensorMap imap;
+  if (!encode_inter_map(ap.inter, (long long)ap.ntx * ap.wy * kTcN, kTcHalf, &imap)) return cudaErrorInvalidValue;
+  const long long nitems = 2ll * ap.ntx * ap.wy;
   long long grid = num_sms > 0 ? num_sms : 1;  // persistent: one CTA per SM
-  if (grid > ntiles) grid = ntiles;
+  if (grid > nitems) grid = nitems;
   if (grid < 1) return cudaSuccess;
-  axial_tc_kernel<<<(unsigned)grid, kTcThreads, smem, s>>>(p);
+  axial_tc_kernel<<<(unsigned)grid, kTcThreads, smem, s>>>(p, imap);
   return cudaGetLastError();
 }
 

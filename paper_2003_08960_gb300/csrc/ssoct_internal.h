@@ -265,6 +265,10 @@ size_t rescale_axial_tile_smem(int nl, int w);
 // Tensor map over a gate's frames seen as uint16 [nl * ny][nx], boxes of
 // box_cols columns x 2 rows (zero fill outside the frame).
 bool encode_frames_map(const Plan& p, const uint16_t* frames, int box_cols, void* map_out);
+// Tensor map over the sweep-axis intermediate seen as float [rows][64] (one
+// row = 32 complex values of one frame of a tile), boxes of box_complex
+// complex values x 256 rows.
+bool encode_inter_map(const float2* inter, long long rows, int box_complex, void* map_out);
 bool lateral_supported(int nx, int ny);
 bool axial_supported(int nl);
 // Tensor-core axial kernel (axial_tc.cu): sweep lengths it handles, its DFT

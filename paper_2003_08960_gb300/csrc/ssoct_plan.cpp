@@ -152,6 +152,19 @@ bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out) {
 }
 
 
+bool encode_inter_map(const float2* inter, long long rows, int box_complex, void* map_out) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)2 * kTile, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kTile * sizeof(float2)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * box_complex), 256};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<float2*>(inter), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool encode_frames_map(const Plan& p, const uint16_t* frames, int box_cols, void* map_out) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
