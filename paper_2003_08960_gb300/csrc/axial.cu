@@ -184,8 +184,12 @@ __global__ void __launch_bounds__(AxStream<NL>::kThreadsAll, 1)
     group_sync<T>(1 + g);  // every thread of the group is done with tile prev's buffer
     if (lt == 0 && prev >= 0 && prev + S::kStages < mine) axial_fill<NL>(p, smem, full_bar, fills, prev + S::kStages);
     if (i >= mine) break;
-    const bool ok = mbar_wait_bounded(&full_bar[i % S::kFull], (unsigned)(i / S::kFull) & 1u, kAxWaitNs);
-    if (!ok) atomicOr(p.err, kErrAxial);
+    // one thread waits for the tile; the others sleep at the group barrier
+    bool ok = true;
+    if (lt == 0) {
+      ok = mbar_wait_bounded(&full_bar[i % S::kFull], (unsigned)(i / S::kFull) & 1u, kAxWaitNs);
+      if (!ok) atomicOr(p.err, kErrAxial);
+    }
     if (group_sync_or<T>(1 + g, !ok)) break;
     float2* ex = reinterpret_cast<float2*>(smem + (size_t)(i % S::kStages) * S::kTileBytes);
     float2 a[N2];
@@ -436,8 +440,12 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
   for (; tile < ntiles; tile += gridDim.x) {
     const int next = tile + gridDim.x;
     records(next, xr, yr);  // in flight while this tile is transformed
-    const bool ok = mbar_wait_bounded(&full, phase & 1u, kAxWaitNs);
-    if (!ok && tid == 0) atomicOr(p.err, kErrAxial);
+    // one thread waits for the copies; the others sleep at the barrier
+    bool ok = true;
+    if (tid == 0) {
+      ok = mbar_wait_bounded(&full, phase & 1u, kAxWaitNs);
+      if (!ok) atomicOr(p.err, kErrAxial);
+    }
     // this tile's rows and records are in; every thread is done with the last tile
     if (__syncthreads_or(!ok)) break;
     pending = false;

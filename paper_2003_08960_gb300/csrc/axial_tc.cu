@@ -275,8 +275,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_group_sync(g);  // every thread of the group is done with item prev's buffer
     if (lt == 0 && prev >= 0 && prev + kTcStages < mine) tc_fill(&imap, ring, full, fills, prev + kTcStages);
     if (i >= mine) break;
-    const bool ok0 = tc_wait(&full[i % kTcFull], (unsigned)(i / kTcFull) & 1u, kTcLoadWaitNs);
-    if (!ok0 && lt == 0) atomicOr(p.err, kErrAxial);
+    // one thread waits for the item; the others sleep at the group barrier
+    bool ok0 = true;
+    if (lt == 0) {
+      ok0 = tc_wait(&full[i % kTcFull], (unsigned)(i / kTcFull) & 1u, kTcLoadWaitNs);
+      if (!ok0) atomicOr(p.err, kErrAxial);
+    }
     if (tc_group_sync_or(g, !ok0)) break;
     unsigned char* buf = ring + (size_t)(i % kTcStages) * kTcItemBytes;
     unsigned short* A = reinterpret_cast<unsigned short*>(buf);  // [hi / lo][block][128 x 32]

@@ -609,9 +609,13 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   for (unsigned s = g;; s += kGroups) {
     const int b = (int)(s % kStages);
     // consumers wait longer than the producer, which gives up first and hands
-    // each group an end mark
-    const bool ok = mbar_wait(&full_bar[s % kFullBars], (s / kFullBars) & 1u, p.ctr,
-                              p.wait_ns ? 2 * p.wait_ns : kConsumerWaitNs);
+    // each group an end mark.  One thread of the group waits; the others sleep
+    // at the group barrier instead of spinning (a spinning group takes issue
+    // slots from the group that has work), and see the buffer's contents
+    // through that barrier.
+    bool ok = true;
+    if (threadIdx.x % kThreads == 0)
+      ok = mbar_wait(&full_bar[s % kFullBars], (s / kFullBars) & 1u, p.ctr, p.wait_ns ? 2 * p.wait_ns : kConsumerWaitNs);
     // the group agrees, and its previous item is finished in all its threads
     if (consumers_sync_or(g, !ok)) break;
     const Desc d = desc[b];
