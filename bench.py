@@ -801,7 +801,11 @@ BATCH_SHAPES = [(256, 256, 64), (384, 384, 96), (512, 512, 128), (512, 512, 128)
 def _batched(args, ss, torch, synth, w_1024, frames_1024, stream, steps=10):
     """Eight uneven volumes (805.8 Mvoxel) reconstructed by one graph launch per
     step (ssoct_batch_run), against the same plans run one after another."""
-    plans, frames, vols = [], [], []
+    import tempfile
+    fd, tune_cache = tempfile.mkstemp(suffix=".json", prefix="ssoct_batch_tune_")
+    os.close(fd)
+    os.unlink(tune_cache)
+    plans, frames, vols, choices = [], [], [], []
     for i, (nx, ny, nl) in enumerate(BATCH_SHAPES):
         if (nx, ny, nl) == (w_1024.nx, w_1024.ny, w_1024.nlambda):
             w, f = w_1024, frames_1024
@@ -811,6 +815,9 @@ def _batched(args, ss, torch, synth, w_1024, frames_1024, stream, steps=10):
         plans.append(ss.Plan(w.nx, w.ny, w.nlambda, w.pitch, w.z, w.lambdas))
         frames.append(f)
         vols.append(plans[-1].empty_volume()[0])
+        # schedule, order and axial form chosen by the library's autotuner (the
+        # two plans of a repeated shape time it once, through a cache file)
+        choices.append(plans[-1].autotune(f, tune_cache, stream))
     voxels = sum(nx * ny * nl for nx, ny, nl in BATCH_SHAPES)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -841,7 +848,10 @@ def _batched(args, ss, torch, synth, w_1024, frames_1024, stream, steps=10):
             p.reconstruct(f, out=(v, None), stream=stream)
 
     ms_sep = timed(separate)
+    if os.path.exists(tune_cache):
+        os.unlink(tune_cache)
     return {"volumes": [f"{nx}x{ny}x{nl}" for nx, ny, nl in BATCH_SHAPES], "voxels": voxels,
+            "autotuned": [{k: c[k] for k in ("lag", "ring_slots", "tc_axial", "axial_first")} for c in choices],
             "ms_per_batch": ms_batch, "Gvoxel_per_s": voxels / (ms_batch * 1e-3) / 1e9,
             "ms_separate": ms_sep, "Gvoxel_per_s_separate": voxels / (ms_sep * 1e-3) / 1e9,
             "lanes": best, "ms_by_lanes": lanes, "graph_captures": captures,

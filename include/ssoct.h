@@ -300,9 +300,10 @@ typedef struct {
 
 /* Time the plan's candidate schedules on frames_dev (reconstructing into the
  * scratch volume vol_dev, [nlambda][wy][wx] float) and keep the fastest: the
- * lateral kernel's (lag, ring slots) with lag 1..3 and lag + 2 <= slots <= the
- * workspace's slots, times the FP32 and tensor-core axial forms when nlambda is
- * 256, in the paper's order and, where the plan offers it, in the axial-first
+ * lateral kernel's (lag, ring slots), lag in {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}
+ * up to nlambda - 1, each with lag + 2, lag + 4 and all of the workspace's
+ * slots (more for smaller frames, whose frames go through the queue faster),
+ * times the FP32 and tensor-core axial forms when nlambda is 256, in the paper's order and, where the plan offers it, in the axial-first
  * order (Eq. 5 + Eq. 7 before Eq. 6, the same V; offered when the frame size
  * has the persistent lateral kernel, nlambda is 64, 128 or 256, the plan has no
  * SSOCT_FLAG_PUPIL, and the half-spectrum planes fit in the sweep-axis

@@ -125,9 +125,11 @@ extern "C" ssoct_status ssoct_autotune(ssoct_plan h, const uint16_t* frames_dev,
 
   // Candidates: the orders the plan offers, times the persistent kernel's
   // schedule (generic-path plans have none), times the axial forms this sweep
-  // length has (paper order).
+  // length has (paper order).  Schedules: lags from 1 up to what the ring
+  // allows, each with the fewest slots it needs (lag + 2), two more, and the
+  // whole ring.
   std::vector<Choice> cand;
-  const int lags[] = {1, 2, 3};
+  const int lags[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
   for (int af = 0; af <= 1; ++af)
     for (int tc = 0; tc <= 1; ++tc) {
       if (p.generic) {
@@ -135,11 +137,16 @@ extern "C" ssoct_status ssoct_autotune(ssoct_plan h, const uint16_t* frames_dev,
         if (valid(p, c)) cand.push_back(c);
         continue;
       }
-      for (int lag : lags)
-        for (int slots = lag + 2; slots <= p.slots_alloc; ++slots) {
+      for (int lag : lags) {
+        const int slot_choices[3] = {lag + 2, lag + 4, p.slots_alloc};
+        for (int i = 0; i < 3; ++i) {
+          const int slots = slot_choices[i];
+          if (i == 1 && slots >= p.slots_alloc) continue;  // the whole ring follows
+          if (i == 2 && slots == lag + 2) continue;
           const Choice c{lag, slots, tc, af};
           if (valid(p, c)) cand.push_back(c);
         }
+      }
     }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return SSOCT_ECUDA;

@@ -121,7 +121,7 @@ bool encode_scratch_map(Plan& p) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const int band = lateral_col_band(p.ny);
-  cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.sch.slots * p.ny};
+  cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.slots_alloc * p.ny};
   cuuint64_t strides[1] = {(cuuint64_t)2 * p.wxp * sizeof(float)};
   cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)(p.ny < 256 ? p.ny : 256)};
   cuuint32_t estr[2] = {1, 1};
@@ -141,7 +141,7 @@ bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const int band = lateral_col_band(p.ny);
-  cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.sch.slots * p.ny};
+  cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.slots_alloc * p.ny};
   cuuint64_t strides[1] = {(cuuint64_t)2 * p.wxp * sizeof(float)};
   cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)(p.ny < 256 ? p.ny : 256)};
   cuuint32_t estr[2] = {1, 1};
@@ -326,7 +326,32 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   // a row item of frame f reuses the slot of frame f - slots, whose last column
   // items were taken four steps earlier: enough slack that the wait is rare
   p.sch.slots = p.sch.lag + 4;
-  p.slots_alloc = p.sch.slots;
+  // Slots the workspace holds (the autotuner may use them all).  A column item
+  // waits for every row item of its frame, so the lag has to span the frames
+  // whose items are in flight at once, about 600 on a 152-SM GPU (two groups
+  // computing and up to two buffers loaded per SM): 2.4 frames of 1024 x 1024,
+  // 9.5 of 512 x 512.  Smaller frames get more slots, as long as the ring
+  // stays within 64 MiB of L2.
+  {
+    const long long items = (long long)p.sch.n_row + p.sch.n_col;
+    const long long in_flight = (600 + items - 1) / items;
+    const long long slot_bytes = (long long)sizeof(float2) * ny * p.wxp;
+    long long n = std::max<long long>(p.sch.slots, in_flight + 4);
+    n = std::min<long long>(n, std::max<long long>(p.sch.slots, (64ll << 20) / slot_bytes));
+    n = std::min<long long>(n, std::max<long long>(p.sch.slots, nlambda));
+    p.slots_alloc = (int)n;
+    // default schedule: a lag of about 0.7 of the frames in flight (what the
+    // autotuner picked at 512 x 512 and 256 x 256; 3 at 1024 x 1024), four
+    // slots of slack
+    if (nlambda >= 3) {
+      const long long lag = std::min<long long>(std::max<long long>(2, (7 * in_flight + 9) / 10),
+                                                std::min<long long>(p.slots_alloc - 4, nlambda - 1));
+      if (lag >= 2) {
+        p.sch.lag = (int)lag;
+        p.sch.slots = (int)lag + 4;
+      }
+    }
+  }
   // input rows a row item stages: from the first row's base to the last row's base + 1
   int st = 0;
   for (int t = 0; t < nlambda; ++t)
@@ -358,7 +383,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_tcb = take(sizeof(unsigned short) * p.tcb.size());
   p.off_wq = take(sizeof(float2) * p.wq.size());
   p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
-  p.off_scratch = take(generic ? 0 : sizeof(float2) * (size_t)p.sch.slots * ny * p.wxp);
+  p.off_scratch = take(generic ? 0 : sizeof(float2) * (size_t)p.slots_alloc * ny * p.wxp);
   const size_t inter_bytes = sizeof(float2) * (size_t)p.wy * p.ntx * nlambda * kTile;
   p.off_inter = take(inter_bytes);
   if (generic) p.off_cg = take(sizeof(float2) * (size_t)nx * ny);

@@ -42,6 +42,11 @@ int main(int argc, char** argv) {
 # frames (lag 2 for k >= 3, else k - 1; slots lag + 4)
 CASES = [(256, 128, 128, 2, 6), (32, 8, 8, 2, 6), (64, 32, 16, 2, 6)]
 CASES += [(256, 128, 128, lag, slots) for lag in (1, 2, 3) for slots in range(lag + 2, 7)]
+# the wider candidates of smaller frames (512 x 512: 32 + 32 items per frame,
+# 14 slots; 256 x 256: 16 + 16 items, 23 slots; 64 x 64: 2 + 2 items, up to nlambda)
+CASES += [(128, 32, 32, lag, slots) for lag in (1, 2, 3, 4, 6, 8, 12) for slots in {lag + 2, lag + 4, 14} if slots >= lag + 2 and slots <= 14]
+CASES += [(64, 16, 16, lag, slots) for lag in (1, 2, 4, 8, 16) for slots in {lag + 2, lag + 4, 23} if slots <= 23]
+CASES += [(256, 2, 2, lag, slots) for lag in (16, 24, 32) for slots in {lag + 2, lag + 4, 156}]
 CASES += [(k, 8, 8, 2 if k >= 3 else k - 1, (2 if k >= 3 else k - 1) + 4) for k in (1, 2, 3, 5, 13, 32)]
 
 
