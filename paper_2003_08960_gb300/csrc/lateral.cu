@@ -131,6 +131,7 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
                                          const float2* twx, const float2* cxs, int g) {
   constexpr int N1 = Split<NX>::N1, N2 = Split<NX>::N2;
   constexpr int RPI = kThreads / N1;
+  static_assert(32 % N1 == 0, "a row's N1 threads lie in one warp");
   const int tid = threadIdx.x % kThreads;
   const int r = tid / N1;
   const int j1 = tid % N1;
@@ -184,7 +185,12 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   Dft<N2, 1>::template run<1, 0>(a);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
-  consumers_sync(g);  // every input of the buffer has been read
+  // every input of the buffer has been read.  In axial-first order row r's
+  // input is its own block of the buffer, read by its own warp only, so the
+  // warp's barrier suffices; otherwise the staged uint16 rows and taps are
+  // shared by the group.
+  if constexpr (AF) __syncwarp();
+  else consumers_sync(g);
   float2* ex = reinterpret_cast<float2*>(buf) + r * NX;  // this row's block (N2 x N1 = NX values)
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) ex[xswz<N1>(k2, j1)] = a[k2];
@@ -409,6 +415,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
           ok = false;
           break;
         }
+        __nanosleep(32);  // leave the issue slots to the consumers meanwhile
       }
       if (ok) {
         __threadfence_block();
