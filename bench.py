@@ -359,7 +359,7 @@ def run_ssoct(args):
                                "|V|^2 volume + 3 cuts per step",
                    "window": [0, 0, wx, wy],
                    "schedule": ({k: tune[k] for k in ("lag", "ring_slots", "tc_axial", "axial_first")} if tune
-                                else "plan default (lag 2, 6 ring slots)"),
+                                else f"plan default (lag {plan.info.ring_slots - 4}, {plan.info.ring_slots} ring slots)"),
                    "form": ("fp32, axial-first order (Eq. 5 + Eq. 7, then Eq. 6 per depth bin)" if af_main
                             else "tensor-core axial (bf16 hi+lo, fp32 accumulate)" if tc_main else "fp32 (paper order)"),
                    "l2": "inputs larger than L2 (512 MiB frames, 2 GiB intermediate per step)"},
