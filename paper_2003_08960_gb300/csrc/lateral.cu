@@ -234,30 +234,36 @@ __device__ __forceinline__ int col_row(int j1, int k2) {
 }
 
 // Axial-first order, end of a column item: V of depth bin q at window column
-// kxw for the rows this thread holds (a[], rows k2 + N2 k1 of the column DFT):
-// |V|^2 |K|^2 (|V| |K| if MAG) into the volume and, if CPLX, V with the output
-// chirp and K into the complex volume.
-template <int NY, bool FW, bool MAG, bool CPLX>
+// kxw for the rows this thread holds (a[], rows k2 + N2 k1 of the column DFT),
+// already scaled by |K| through the input chirp: |V|^2 |K|^2 (|V| |K| if MAG)
+// into the volume and, if CPLX, V with the output chirp and K into the complex
+// volume.  Full-window plans use the frame's sizes as the volume's strides, so
+// that the stores take constant offsets.
+template <int NY, bool FW, bool MAG, bool CPLX, int NX>
 __device__ __forceinline__ void af_epilogue(const LateralParams& p, const Desc& d, const float2* a, int j1,
                                             int kxw) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
   const int q = af_bin(d.f, p.nl);
-  float* vdst = p.vol + (size_t)q * p.wy * p.wx + kxw;
+  const int wx = FW ? NX : p.wx, wy = FW ? NY : p.wy;
+  float* vdst = p.vol + (size_t)q * wy * wx + kxw;
   float2 ox = make_float2(0.f, 0.f);
-  if constexpr (CPLX) ox = ldg2(p.ox + kxw);
+  if constexpr (CPLX) {
+    ox = ldg2(p.ox + kxw);
+    ox = make_float2(ox.x * p.inv_k_abs, ox.y * p.inv_k_abs);
+  }
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       const int kyw = k2 + N2 * k1 - (FW ? 0 : p.y0);
-      if (FW || (kyw >= 0 && kyw < p.wy)) {
+      if (FW || (kyw >= 0 && kyw < wy)) {
         const float2 v = a[i * N1 + k1];
-        float pw = fmaf(v.x, v.x, v.y * v.y) * p.power_scale;
+        float pw = fmaf(v.x, v.x, v.y * v.y);
         if constexpr (MAG) pw = sqrtf(pw);
-        __stcs(vdst + (size_t)kyw * p.wx, pw);
+        __stcs(vdst + (size_t)kyw * wx, pw);
         if constexpr (CPLX)
-          __stcs(p.cplx + ((size_t)q * p.wy + kyw) * p.wx + kxw, cmul(v, cmul(ox, ldg2(p.oy + kyw))));
+          __stcs(p.cplx + ((size_t)q * wy + kyw) * wx + kxw, cmul(v, cmul(ox, ldg2(p.oy + kyw))));
       }
     }
   });
@@ -267,7 +273,7 @@ __device__ __forceinline__ void af_epilogue(const LateralParams& p, const Desc& 
 // buffer holds the band [NY][BC] copied from the scratch slot; the first DFT
 // pass writes back in place (up to the row-pair swap of col_row), the second
 // stores the item's outputs straight from registers.
-template <int NY, bool FW, bool AF>
+template <int NX, int NY, bool FW, bool AF>
 __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, unsigned char* buf,
                                          const float2* twy, int g) {
   constexpr int N1 = Split<NY>::N1, N2 = Split<NY>::N2;
@@ -311,11 +317,11 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
     const int kxw = d.item * BC + b;  // column bands already span the window's columns
     if (kxw < p.wx) {
       if (p.cplx) {
-        if (p.magnitude) af_epilogue<NY, FW, true, true>(p, d, a, j1, kxw);
-        else af_epilogue<NY, FW, false, true>(p, d, a, j1, kxw);
+        if (p.magnitude) af_epilogue<NY, FW, true, true, NX>(p, d, a, j1, kxw);
+        else af_epilogue<NY, FW, false, true, NX>(p, d, a, j1, kxw);
       } else {
-        if (p.magnitude) af_epilogue<NY, FW, true, false>(p, d, a, j1, kxw);
-        else af_epilogue<NY, FW, false, false>(p, d, a, j1, kxw);
+        if (p.magnitude) af_epilogue<NY, FW, true, false, NX>(p, d, a, j1, kxw);
+        else af_epilogue<NY, FW, false, false, NX>(p, d, a, j1, kxw);
       }
     }
   } else {
@@ -605,6 +611,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   for (int i = tid; i < NX; i += kGroups * kThreads) {
     twx[i] = ldg2(p.twx + i);
     cxs[i] = ldg2(p.cx + i);
+    if constexpr (AF) cxs[i] = make_float2(cxs[i].x * p.k_abs, cxs[i].y * p.k_abs);
   }
   for (int i = tid; i < NY; i += kGroups * kThreads) twy[i] = ldg2(p.twy + i);
   asm volatile("bar.sync 3, %0;" ::"n"(kGroups * kThreads) : "memory");  // tables seen by both groups
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
     if (d.kind == kRowItem)
       row_item<NX, NY, FW, AF>(p, d, buf, twx, cxs, g);
     else
-      col_item<NY, FW, AF>(p, d, buf, twy, g);
+      col_item<NX, NY, FW, AF>(p, d, buf, twy, g);
     // this thread's writes to the buffer come before its next TMA fill (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_arrive(&done_bar[b]);

@@ -139,7 +139,8 @@ struct LateralParams {
   float2* cplx;            // optional [nl][wy][wx]
   const float2* ox;        // [wx] output chirp (x)
   const float2* oy;        // [wy] output chirp (y) times K
-  float power_scale;       // |K|^2
+  float k_abs;             // |K|, folded into the input chirp of the row items (so |V|^2 |K|^2 = |v|^2)
+  float inv_k_abs;         // 1 / |K|, taken back out of the complex output (oy already holds K)
   int magnitude;
 };
 

@@ -638,7 +638,8 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
     lp.cplx = (float2*)cplx;
     lp.ox = (const float2*)(p.ws + p.off_ox);
     lp.oy = (const float2*)(p.ws + p.off_oy);
-    lp.power_scale = (float)(p.alpha * p.alpha);
+    lp.k_abs = (float)p.alpha;
+    lp.inv_k_abs = (float)(1.0 / p.alpha);
     lp.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
   }
   cudaEvent_t* ev = nullptr;
