@@ -241,6 +241,9 @@ struct RescaleAxialParams {
   const Tap* ytab;         // [nl][ny]
   const float2* twl;       // [N2l][N1l], sign -
   float2* planes;          // [nl/2 + 1][ny][nx]
+  const float2* cx;        // [nx] input chirp of Eq. 6 (with the centring phase)
+  const float2* cy;        // [ny]
+  float k_abs;             // |K| of Eq. 6
   int nx, ny, nl;
 };
 
@@ -249,7 +252,9 @@ struct RescaleAxialParams {
 // transform over t, and bins q = 0 .. nl/2 as complex planes.  The rest of the
 // spectrum is the conjugate mirror (real input) and is formed by the lateral
 // pass.  Eq. 6 is linear and the same for every frame, so transforming over t
-// before it gives the same V as the paper's order.
+// before it gives the same V as the paper's order.  The planes are stored times
+// the input chirp of Eq. 6 and |K| (X c |K|): bins up to nl/2 then enter the
+// lateral pass's DFTs as they are, and the mirrored bins take c^2 there.
 template <int NL>
 __global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(const __grid_constant__ RescaleAxialParams p) {
   constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
@@ -281,13 +286,15 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(co
   });
   const size_t plane = (size_t)p.ny * p.nx;
   float2* dst = p.planes + (size_t)y * p.nx + x;
+  float2 c = cmul(ldg2(p.cx + x), ldg2(p.cy + y));
+  c = make_float2(c.x * p.k_abs, c.y * p.k_abs);
   static_for<0, N2 / N1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       const int q = k2 + N2 * k1;
-      if (q <= NL / 2) dst[(size_t)q * plane] = a[i * N1 + k1];
+      if (q <= NL / 2) dst[(size_t)q * plane] = cmul(a[i * N1 + k1], c);
     }
   });
 }
@@ -326,6 +333,9 @@ struct RescaleAxialTileParams {
   const Tap* ytab;           // [nl][ny]
   const float2* twl;         // [N2l][N1l], sign -
   float2* planes;            // [nl/2 + 1][ny][nx]
+  const float2* cx;          // [nx] input chirp of Eq. 6 (with the centring phase)
+  const float2* cy;          // [ny]
+  float k_abs;               // |K| of Eq. 6
   int nx, ny, w;             // w: staged columns per source row (multiple of 8)
   unsigned* err;             // kErrAxial is ORed in if a staging wait runs out
 };
@@ -482,8 +492,16 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
       for (int k1 = 0; k1 < N1; ++k1) ex[(k2 * N1 + k1) * 32 + pp] = a[i * N1 + k1];
     });
     __syncthreads();
-    // 3. the two real series' spectra, bins q = 0 .. NL/2, as plane rows
-    float2* dst = p.planes + (size_t)y * p.nx + strip * kRaStrip + pp;
+    // 3. the two real series' spectra, bins q = 0 .. NL/2, as plane rows, times
+    //    the input chirp and |K| of Eq. 6 at their pixels (the factor 1/2 of the
+    //    separation folded in)
+    const int xa = strip * kRaStrip + pp;
+    float2* dst = p.planes + (size_t)y * p.nx + xa;
+    const float2 cyv = ldg2(p.cy + y);
+    const float h = 0.5f * p.k_abs;
+    float2 ca = cmul(ldg2(p.cx + xa), cyv), cb = cmul(ldg2(p.cx + xa + 32), cyv);
+    ca = make_float2(ca.x * h, ca.y * h);
+    cb = make_float2(cb.x * h, cb.y * h);
     static_for<0, N2 / N1>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const int k2 = j1 + N1 * i;
@@ -494,8 +512,8 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
           const int qm = (NL - q) % NL;
           const float2 zq = a[i * N1 + k1];
           const float2 zm = ex[((qm % N2) * N1 + qm / N2) * 32 + pp];
-          __stcs(dst + (size_t)q * plane, make_float2(0.5f * (zq.x + zm.x), 0.5f * (zq.y - zm.y)));
-          __stcs(dst + (size_t)q * plane + 32, make_float2(0.5f * (zq.y + zm.y), 0.5f * (zm.x - zq.x)));
+          __stcs(dst + (size_t)q * plane, cmul(make_float2(zq.x + zm.x, zq.y - zm.y), ca));
+          __stcs(dst + (size_t)q * plane + 32, cmul(make_float2(zq.y + zm.y, zm.x - zq.x), cb));
         }
       }
     });
@@ -771,6 +789,9 @@ cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring
     tp.ytab = (const Tap*)(p.ws + p.off_ytab);
     tp.twl = (const float2*)(p.ws + p.off_twl);
     tp.planes = planes;
+    tp.cx = (const float2*)(p.ws + p.off_cx);
+    tp.cy = (const float2*)(p.ws + p.off_cy);
+    tp.k_abs = (float)p.alpha;
     tp.nx = p.nx;
     tp.ny = p.ny;
     tp.w = p.ra_w;
@@ -787,6 +808,9 @@ cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring
   rp.ytab = (const Tap*)(p.ws + p.off_ytab);
   rp.twl = (const float2*)(p.ws + p.off_twl);
   rp.planes = planes;
+  rp.cx = (const float2*)(p.ws + p.off_cx);
+  rp.cy = (const float2*)(p.ws + p.off_cy);
+  rp.k_abs = (float)p.alpha;
   rp.nx = p.nx;
   rp.ny = p.ny;
   rp.nl = p.nl;

@@ -143,27 +143,27 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   const float2* ychirp = reinterpret_cast<const float2*>(ytaps + RPI);
   // 1. Eq. 5 resample (taps outside the frame carry weight 0) x input chirp,
   //    elements n = j1 + N1 * j2 of row y; in axial-first order the row of the
-  //    half-spectrum plane of bin q (conjugated for q > N/2) x input chirp
+  //    half-spectrum plane of bin q, which already carries the input chirp c
+  //    (and |K|), as it is for q <= N/2 and conjugated x c^2 above
   float2 a[N2];
   float2 cyv;
+  bool mirrored = false;
   if constexpr (AF) {
     const float2* in2 = reinterpret_cast<const float2*>(buf) + r * NX;
-    // bins above N/2 use the conjugate plane: conj(v) c = (v.x c.x + v.y c.y, v.x c.y - v.y c.x)
-    if (af_bin(f, p.nl) > p.nl / 2) {
+    mirrored = af_bin(f, p.nl) > p.nl / 2;
+    if (mirrored) {
+      // conj(v) c2 = (v.x c2.x + v.y c2.y, v.x c2.y - v.y c2.x); cxs holds c2 in this order
 #pragma unroll
       for (int j2 = 0; j2 < N2; ++j2) {
         const int n = j1 + N1 * j2;
         const float2 v = in2[n], c = cxs[n];
         a[j2] = make_float2(fmaf(v.x, c.x, v.y * c.y), fmaf(v.x, c.y, -v.y * c.x));
       }
+      cyv = ldg2(p.cy2 + y);
     } else {
 #pragma unroll
-      for (int j2 = 0; j2 < N2; ++j2) {
-        const int n = j1 + N1 * j2;
-        a[j2] = cmul(in2[n], cxs[n]);
-      }
+      for (int j2 = 0; j2 < N2; ++j2) a[j2] = in2[j1 + N1 * j2];
     }
-    cyv = ldg2(p.cy + y);
   } else {
     cyv = ychirp[r];
     const Tap ty = ytaps[r];
@@ -181,10 +181,16 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
     }
   }
   // 2. row DFT (+ sign of Eq. 6): N2-point DFT in registers, twiddle with the
-  //    row's y chirp folded in, transpose in the stage buffer, N1-point DFTs
+  //    row's y chirp folded in (none for the planes' own bins in axial-first
+  //    order), transpose in the stage buffer, N1-point DFTs
   Dft<N2, 1>::template run<1, 0>(a);
+  if (AF && !mirrored) {
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
+    for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], twx[k2 * N1 + j1]);
+  } else {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) a[k2] = cmul(a[k2], cmul(twx[k2 * N1 + j1], cyv));
+  }
   // every input of the buffer has been read.  In axial-first order row r's
   // input is its own block of the buffer, read by its own warp only, so the
   // warp's barrier suffices; otherwise the staged uint16 rows and taps are
@@ -235,7 +241,7 @@ __device__ __forceinline__ int col_row(int j1, int k2) {
 
 // Axial-first order, end of a column item: V of depth bin q at window column
 // kxw for the rows this thread holds (a[], rows k2 + N2 k1 of the column DFT),
-// already scaled by |K| through the input chirp: |V|^2 |K|^2 (|V| |K| if MAG)
+// already scaled by |K| through the planes: |V|^2 |K|^2 (|V| |K| if MAG)
 // into the volume and, if CPLX, V with the output chirp and K into the complex
 // volume.  Full-window plans use the frame's sizes as the volume's strides, so
 // that the stores take constant offsets.
@@ -610,8 +616,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1)
   }
   for (int i = tid; i < NX; i += kGroups * kThreads) {
     twx[i] = ldg2(p.twx + i);
-    cxs[i] = ldg2(p.cx + i);
-    if constexpr (AF) cxs[i] = make_float2(cxs[i].x * p.k_abs, cxs[i].y * p.k_abs);
+    cxs[i] = ldg2((AF ? p.cx2 : p.cx) + i);  // axial-first order: the squared chirp, for the mirrored bins
   }
   for (int i = tid; i < NY; i += kGroups * kThreads) twy[i] = ldg2(p.twy + i);
   asm volatile("bar.sync 3, %0;" ::"n"(kGroups * kThreads) : "memory");  // tables seen by both groups

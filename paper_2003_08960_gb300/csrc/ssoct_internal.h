@@ -121,6 +121,8 @@ struct LateralParams {
   const Tap* ytab;         // [nl][ny]
   const float2* cx;        // [nx] input chirp incl. centring phase
   const float2* cy;        // [ny]
+  const float2* cx2;       // [nx] squared input chirp (axial-first order, bins above nl/2)
+  const float2* cy2;       // [ny]
   const float2* twx;       // [N2x][N1x] row-FFT twiddles
   const float2* twy;       // [N2y][N1y] column-FFT twiddles
   float2* scratch;         // [slots][ny][wxp]
@@ -139,8 +141,7 @@ struct LateralParams {
   float2* cplx;            // optional [nl][wy][wx]
   const float2* ox;        // [wx] output chirp (x)
   const float2* oy;        // [wy] output chirp (y) times K
-  float k_abs;             // |K|, folded into the input chirp of the row items (so |V|^2 |K|^2 = |v|^2)
-  float inv_k_abs;         // 1 / |K|, taken back out of the complex output (oy already holds K)
+  float inv_k_abs;         // 1 / |K|: the planes carry |K| (so |V|^2 |K|^2 = |v|^2), oy holds K as well
   int magnitude;
 };
 
@@ -176,7 +177,7 @@ struct Plan {
   double alpha;             // d^2 / (lambda_1 z) = |K|
   // host tables
   std::vector<Tap> xtab, ytab;
-  std::vector<float2> cx, cy, ox, oy, twx, twy, twl;
+  std::vector<float2> cx, cy, cx2, cy2, ox, oy, twx, twy, twl;
   std::vector<float2> wq;   // [nl] exp(-2 pi i k / nl), for single-bin transforms
   std::vector<unsigned short> tcb;  // SSOCT_FLAG_TC_AXIAL: BF16 hi / lo 16-point DFT matrix (operand layout)
   // SSOCT_FLAG_PUPIL: input chirp x Zernike screen, its distance z and |K|, frames per Q chunk
@@ -195,7 +196,7 @@ struct Plan {
   int slots_alloc = 0;       // scratch-ring slots the workspace holds (sch.slots <= slots_alloc)
   bool use_tc = false;       // axial pass on the tensor cores (flag, or the autotuner's choice)
   // workspace layout (byte offsets)
-  size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_ox, off_oy, off_twx, off_twy, off_twl;
+  size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_cx2, off_cy2, off_ox, off_oy, off_twx, off_twy, off_twl;
   size_t off_tcb, off_wq, off_ring, off_scratch, off_inter, ws_bytes;
   size_t off_cp = 0, off_F = 0, off_Q = 0, off_red = 0;  // SSOCT_FLAG_PUPIL regions
   // Frame sizes the persistent lateral kernel does not compile (384, 640, 768)

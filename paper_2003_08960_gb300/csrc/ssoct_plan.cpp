@@ -76,6 +76,18 @@ std::vector<float2> input_chirp(int n, double alpha) {
   return v;
 }
 
+// Square of the input chirp: exp(-2 i pi (k - n/2)^2 alpha) (the centring
+// phase squares to 1).  In axial-first order the planes carry the input chirp
+// c, and a bin above nl/2 needs conj(X) c = conj(X c) c^2.
+std::vector<float2> input_chirp_squared(int n, double alpha) {
+  std::vector<float2> v(n);
+  for (int k = 0; k < n; ++k) {
+    const double d = k - n / 2.0;
+    v[k] = cis_pi(-std::fmod(2.0 * d * d * alpha, 2.0));
+  }
+  return v;
+}
+
 // Output chirp of Eq. 6 on the hologram grid x_m = (m - n/2) d', times the
 // remaining centring phase exp(-i pi (m - n/2)):  exp(-i pi [(m - n/2)^2 / (n^2 alpha) + m - n/2]).
 std::vector<float2> output_chirp(int n, double alpha, int m0, int count) {
@@ -287,6 +299,8 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   // Eq. 6 chirps.  alpha x (k - n/2)^2 is the chirp phase / pi.
   p.cx = input_chirp(nx, p.alpha);
   p.cy = input_chirp(ny, p.alpha);
+  p.cx2 = input_chirp_squared(nx, p.alpha);
+  p.cy2 = input_chirp_squared(ny, p.alpha);
   p.ox = output_chirp(nx, p.alpha, p.x0, p.wx);
   {
     std::vector<float2> oy = output_chirp(ny, p.alpha, p.y0, p.wy);
@@ -375,6 +389,8 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_ytab = take(sizeof(Tap) * p.ytab.size());
   p.off_cx = take(sizeof(float2) * nx);
   p.off_cy = take(sizeof(float2) * ny);
+  p.off_cx2 = take(sizeof(float2) * nx);
+  p.off_cy2 = take(sizeof(float2) * ny);
   p.off_ox = take(sizeof(float2) * p.wx);
   p.off_oy = take(sizeof(float2) * p.wy);
   p.off_twx = take(sizeof(float2) * p.twx.size());
@@ -450,6 +466,8 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
       {p.off_ytab, p.ytab.data(), sizeof(Tap) * p.ytab.size()},
       {p.off_cx, p.cx.data(), sizeof(float2) * p.cx.size()},
       {p.off_cy, p.cy.data(), sizeof(float2) * p.cy.size()},
+      {p.off_cx2, p.cx2.data(), sizeof(float2) * p.cx2.size()},
+      {p.off_cy2, p.cy2.data(), sizeof(float2) * p.cy2.size()},
       {p.off_ox, p.ox.data(), sizeof(float2) * p.ox.size()},
       {p.off_oy, p.oy.data(), sizeof(float2) * p.oy.size()},
       {p.off_twx, p.twx.data(), sizeof(float2) * p.twx.size()},
@@ -546,6 +564,8 @@ static LateralParams lateral_params(const Plan& p, const uint16_t* frames, int r
   lp.ytab = (const Tap*)(ws + p.off_ytab);
   lp.cx = (const float2*)(ws + p.off_cx);
   lp.cy = (const float2*)(ws + p.off_cy);
+  lp.cx2 = (const float2*)(ws + p.off_cx2);
+  lp.cy2 = (const float2*)(ws + p.off_cy2);
   lp.twx = (const float2*)(ws + p.off_twx);
   lp.twy = (const float2*)(ws + p.off_twy);
   lp.scratch = (float2*)(ws + p.off_scratch);
@@ -638,7 +658,6 @@ static ssoct_status run_volume(Plan& p, const uint16_t* frames, int ring_start, 
     lp.cplx = (float2*)cplx;
     lp.ox = (const float2*)(p.ws + p.off_ox);
     lp.oy = (const float2*)(p.ws + p.off_oy);
-    lp.k_abs = (float)p.alpha;
     lp.inv_k_abs = (float)(1.0 / p.alpha);
     lp.magnitude = (p.flags & SSOCT_FLAG_MAGNITUDE) ? 1 : 0;
   }
