@@ -135,7 +135,8 @@ struct TcParams {
   const float2* ox;
   const float2* oy;
   int wx, wy, ntx;
-  float power_scale;
+  float k_abs;                  // |K|, folded into the stage-2 twiddles (so |V|^2 |K|^2 = |v|^2)
+  float inv_k_abs;              // 1 / |K|, taken back out of the complex output (oy holds K)
   int magnitude;
   unsigned* err;                // kErrAxialTc (MMA wait) / kErrAxial (tile wait) ORed in on a time-out
 };
@@ -210,7 +211,8 @@ __device__ __forceinline__ void tc_issue_stage(unsigned tmem, const unsigned sho
 }
 
 // |V|^2 |K|^2 (|V| |K| if MAG) of the 16 depth bins q = k2 + 16 k1 this thread
-// holds into the item's output rows; with CPLX also V with the output chirp and K.
+// holds (v carries |K| from the twiddles) into the item's output rows; with
+// CPLX also V with the output chirp and K.
 template <bool MAG, bool CPLX>
 __device__ __forceinline__ void tc_epilogue(const TcParams& p, const float (&v)[32], float* out, int k2, int px,
                                             int kx0, int kyw) {
@@ -218,12 +220,13 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, const float (&v)[
   float2 of = make_float2(0.f, 0.f);
   if constexpr (CPLX) {
     if (in) of = cmul(ldg2(p.ox + kx0 + px), ldg2(p.oy + kyw));
+    of = make_float2(of.x * p.inv_k_abs, of.y * p.inv_k_abs);
   }
 #pragma unroll
   for (int k1 = 0; k1 < 16; ++k1) {
     const int q = k2 + 16 * k1;
     const float2 x = make_float2(v[2 * k1], v[2 * k1 + 1]);
-    float pw = fmaf(x.x, x.x, x.y * x.y) * p.power_scale;
+    float pw = fmaf(x.x, x.x, x.y * x.y);
     if constexpr (MAG) pw = sqrtf(pw);
     out[q * kOutStride + px] = pw;
     if constexpr (CPLX) {
@@ -262,7 +265,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int t = 0; t < kTcStages && t < mine; ++t) tc_fill(&imap, ring, full, fills, t);
   }
   if (tid < 256) reinterpret_cast<uint4*>(Bs)[tid] = __ldg(reinterpret_cast<const uint4*>(p.bmat) + tid);  // 4 KB
-  if (tid < kTcN) tw[tid] = ldg2(p.twl + tid);
+  if (tid < kTcN) {
+    const float2 t = ldg2(p.twl + tid);
+    tw[tid] = make_float2(t.x * p.k_abs, t.y * p.k_abs);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -478,7 +484,8 @@ cudaError_t launch_axial_tc(const Plan& pl, const AxialParams& ap, const unsigne
   p.wx = ap.wx;
   p.wy = ap.wy;
   p.ntx = ap.ntx;
-  p.power_scale = ap.power_scale;
+  p.k_abs = (float)std::sqrt((double)ap.power_scale);
+  p.inv_k_abs = (float)(1.0 / std::sqrt((double)ap.power_scale));
   p.magnitude = ap.magnitude;
   p.err = err;
   const size_t smem = axial_tc_smem_bytes();
