@@ -24,9 +24,14 @@
 //    signalled, load the band from the scratch slot, run the Ny-point column DFT
 //    the same way, keep the window rows and write them into the sweep-axis
 //    intermediate [wy][tile][t][32] that the axial kernel streams.
-// The scratch ring holds `slots` frames, so the row-transformed frames never
-// leave L2: only the uint16 input is read from HBM and only the windowed
-// complex hologram is written to it.
+// The scratch ring holds `slots` frames, so that most row-transformed frames
+// are read back from L2: the uint16 input is read from HBM once and the
+// windowed complex hologram written to it (lines of the ring evicted dirty
+// after their column items are written back as well).
+// Axial-first order (AF): frame f is depth bin af_bin(f); row items read rows
+// of the half-spectrum plane of that bin, which the first pass stored times
+// the input chirp and |K| (bins above N/2 take the plane conjugated, times the
+// squared chirp), and column items write |V|^2 straight into the volume.
 #include <cuda.h>
 
 #include "fft_common.cuh"
@@ -124,8 +129,8 @@ __device__ __forceinline__ float u16_to_f(unsigned short u) {
 }
 
 // Row item: rows [item*RPI, item*RPI + RPI) of frame d.f.  The stage buffer holds
-// input rows jlo .. jlo + nrows - 1 (uint16) and the taps; it then serves as the
-// transpose block and, for whole-frame plans, as the output [RPI][NX].
+// input rows jlo .. jlo + nrows - 1 (uint16) and the taps (in axial-first
+// order the RPI plane rows); it then serves as the transpose block.
 template <int NX, int NY, bool FW, bool AF>
 __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, unsigned char* buf,
                                          const float2* twx, const float2* cxs, int g) {
