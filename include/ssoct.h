@@ -98,9 +98,9 @@ typedef struct {
 
 /* Create a plan.  Host only: no CUDA call is made here.
  *   nx, ny     frame size (pixels).  The persistent lateral kernel compiles
- *              nx, ny in {64, 128, 256, 512, 1024} (square), plus (128, 64) and
- *              (64, 128).  Any other pair from {64, 128, 256, 384, 512, 640,
- *              768, 1024} (mixed radix 2/3/5) takes a two-pass lateral path
+ *              nx, ny in {64, 128, 256, 384, 512, 640, 768, 1024} (square),
+ *              plus (128, 64) and (64, 128).  Any other pair from that set
+ *              (mixed radix 2/3/5) takes a two-pass lateral path
  *              (row pass, column pass through a frame buffer in the
  *              workspace); such plans do not offer ssoct_reconstruct_sliding
  *              or ssoct_reconstruct_frames_noalloc (EUNSUPPORTED there).

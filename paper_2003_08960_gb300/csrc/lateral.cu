@@ -128,6 +128,19 @@ __device__ __forceinline__ float u16_to_f(unsigned short u) {
   return __uint2float_rn((unsigned)u);
 }
 
+// Stage 2 of a transform of length N = N1 x N2: N2 N1-point DFTs spread over
+// the transform's N1 threads, NI per thread; where N1 does not divide N2
+// (384 = 16 x 24, 640 = 32 x 20, 768 = 32 x 24) the last one is idle in the
+// threads j1 >= N2 - N1 (NI - 1).  A is the register array length.
+template <int N>
+struct Stage2 {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int NI = (N2 + N1 - 1) / N1;
+  static constexpr int A = NI * N1 > N2 ? NI * N1 : N2;
+  // stage-2 DFT i of thread j1 exists (always, for the iterations N1 fills)
+  __device__ __forceinline__ static bool live(int i, int j1) { return (i + 1) * N1 <= N2 || j1 + N1 * i < N2; }
+};
+
 // Row item: rows [item*RPI, item*RPI + RPI) of frame d.f.  The stage buffer holds
 // input rows jlo .. jlo + nrows - 1 (uint16) and the taps (in axial-first
 // order the RPI plane rows); it then serves as the transpose block.
@@ -150,7 +163,8 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
   //    elements n = j1 + N1 * j2 of row y; in axial-first order the row of the
   //    half-spectrum plane of bin q, which already carries the input chirp c
   //    (and |K|), as it is for q <= N/2 and conjugated x c^2 above
-  float2 a[N2];
+  using S2 = Stage2<NX>;
+  float2 a[S2::A];
   float2 cyv;
   bool mirrored = false;
   if constexpr (AF) {
@@ -206,20 +220,23 @@ __device__ __forceinline__ void row_item(const LateralParams& p, const Desc& d, 
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) ex[xswz<N1>(k2, j1)] = a[k2];
   __syncwarp();  // a row's N1 threads lie in one warp
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, S2::NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (S2::live(i, j1)) {
 #pragma unroll
-    for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[xswz<N1>(k2, jj)];
-    Dft<N1, 1>::template run<1, i * N1>(a);
+      for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[xswz<N1>(k2, jj)];
+      Dft<N1, 1>::template run<1, i * N1>(a);
+    }
   });
   {
     // 3. window columns straight into the scratch slot of frame f
     const unsigned long long pol_last = policy_evict_last();
     float2* dst = p.scratch + ((size_t)(f % p.sch.slots) * NY + y) * p.wxp;
-    static_for<0, N2 / N1>([&](auto I) {
+    static_for<0, S2::NI>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const int k2 = j1 + N1 * i;
+      if (!S2::live(i, j1)) return;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
         if constexpr (FW) {
@@ -262,9 +279,10 @@ __device__ __forceinline__ void af_epilogue(const LateralParams& p, const Desc& 
     ox = ldg2(p.ox + kxw);
     ox = make_float2(ox.x * p.inv_k_abs, ox.y * p.inv_k_abs);
   }
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, Stage2<NY>::NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (!Stage2<NY>::live(i, j1)) return;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       const int kyw = k2 + N2 * k1 - (FW ? 0 : p.y0);
@@ -294,7 +312,8 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
   const int b = tid % BC;
   const int j1 = tid / BC;
   float2* tile = reinterpret_cast<float2*>(buf);
-  float2 a[N2];
+  using S2 = Stage2<NY>;
+  float2 a[S2::A];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) a[j2] = tile[(j1 + N1 * j2) * BC + b];
   Dft<N2, 1>::template run<1, 0>(a);
@@ -304,9 +323,10 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) tile[col_row<N1, BC>(j1, k2) * BC + b] = a[k2];
   consumers_sync(g);
-  static_for<0, N2 / N1>([&](auto I) {
+  static_for<0, S2::NI>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int k2 = j1 + N1 * i;
+    if (!S2::live(i, j1)) return;
     if constexpr (BC == 8) {
       // row jj ^ sw: jj + sw for even jj, jj - sw for odd jj (two bases, constant offsets)
       const int sw = k2 & 1;
@@ -341,9 +361,10 @@ __device__ __forceinline__ void col_item(const LateralParams& p, const Desc& d, 
       const unsigned long long pol_first = policy_evict_first();
       float2* dst = p.inter + (size_t)(kxw / kTile) * p.nl * kTile + (size_t)d.slot * kTile + (kxw % kTile);
       const size_t row_pitch = (size_t)p.ntx * p.nl * kTile;
-      static_for<0, N2 / N1>([&](auto I) {
+      static_for<0, S2::NI>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const int k2 = j1 + N1 * i;
+        if (!S2::live(i, j1)) return;
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
           if constexpr (FW) {
@@ -402,7 +423,7 @@ __device__ void producer(const LateralParams& p, const CUtensorMap* tmap, uint64
                          unsigned char* stage0, Handover* ho, int pi) {
   constexpr int RPI = kThreads / Split<NX>::N1;
   constexpr int BC = kThreads / Split<NY>::N1;
-  constexpr int BOX_ROWS = NY < 256 ? NY : 256;
+  constexpr int BOX_ROWS = band_box_rows(NY);
   const unsigned total = (unsigned)p.sch.total();
   auto give_up = [&]() {
     atomicCAS(&p.ctr->err, 0u, kErrTimeout);
@@ -588,8 +609,7 @@ template <int NX, int NY, bool FW, bool AF>
 __global__ void __launch_bounds__(kCtaThreads, 1)
     lateral_kernel(const __grid_constant__ LateralParams p, const __grid_constant__ CUtensorMap tmap) {
   static_assert(kThreads / Split<NX>::N1 <= NY, "a row item must not exceed the frame");
-  static_assert(Split<NX>::N2 % Split<NX>::N1 == 0 && Split<NY>::N2 % Split<NY>::N1 == 0,
-                "the second stage needs N1 | N2");
+  static_assert(NY % band_box_rows(NY) == 0, "whole tensor copies cover a column band");
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full_bar[kFullBars];
   __shared__ __align__(8) uint64_t done_bar[kStages];
@@ -709,7 +729,7 @@ cudaError_t launch(const Plan& p, const LateralParams& lp, const void* tmap, int
 }
 
 #define SSOCT_LATERAL_SIZES(X) \
-  X(64, 64) X(128, 128) X(256, 256) X(512, 512) X(1024, 1024) X(128, 64) X(64, 128)
+  X(64, 64) X(128, 128) X(256, 256) X(384, 384) X(512, 512) X(640, 640) X(768, 768) X(1024, 1024) X(128, 64) X(64, 128)
 
 }  // namespace
 

@@ -21,6 +21,14 @@ __host__ __device__ constexpr int split_n1(int n) {
        : n == 256 ? 16 : n == 384 ? 16 : n == 512 ? 16 : n == 640 ? 32 : n == 768 ? 32 : n == 1024 ? 32 : 0;
 }
 
+// Rows per tensor copy of a lateral column band: the largest divisor of ny up
+// to 256 (a box dimension's limit), so that whole boxes cover the column.
+__host__ __device__ constexpr int band_box_rows(int ny) {
+  int r = ny < 256 ? ny : 256;
+  while (r > 1 && ny % r != 0) --r;
+  return r;
+}
+
 // Separable linear-interpolation tap for one output coordinate of one frame
 // (Eq. 5): the value is w0 * in[base] + w1 * in[base + 1]; base is clamped so
 // both reads are inside the frame, and a weight is 0 where its tap fell outside.

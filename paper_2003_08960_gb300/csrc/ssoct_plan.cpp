@@ -128,14 +128,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // Tensor map over the scratch ring seen as float32 [slots * ny][2 * wxp]; one
-// box is a column band of the lateral kernel (2 * band floats x min(ny, 256) rows).
+// box is a column band of the lateral kernel (2 * band floats x band_box_rows(ny) rows).
 bool encode_scratch_map(Plan& p) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const int band = lateral_col_band(p.ny);
   cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.slots_alloc * p.ny};
   cuuint64_t strides[1] = {(cuuint64_t)2 * p.wxp * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)(p.ny < 256 ? p.ny : 256)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)band_box_rows(p.ny)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(reinterpret_cast<CUtensorMap*>(p.tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.ws + p.off_scratch,
                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -155,7 +155,7 @@ bool encode_scratch_map_at(const Plan& p, void* scratch_dev, void* map_out) {
   const int band = lateral_col_band(p.ny);
   cuuint64_t dims[2] = {(cuuint64_t)2 * p.wxp, (cuuint64_t)p.slots_alloc * p.ny};
   cuuint64_t strides[1] = {(cuuint64_t)2 * p.wxp * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)(p.ny < 256 ? p.ny : 256)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * band), (cuuint32_t)band_box_rows(p.ny)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, scratch_dev, dims,
                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -70,6 +70,9 @@ def test_create_plan_validation(ss):
     assert st == ss.SSOCT_OK
     ss.ssoct_destroy_plan(h)
     st, h = ss.ssoct_create_plan(384, 384, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_AXIAL_FIRST)
+    assert st == ss.SSOCT_OK
+    ss.ssoct_destroy_plan(h)
+    st, h = ss.ssoct_create_plan(640, 384, 32, 20e-6, 0.3, LAM, flags=ss.SSOCT_FLAG_AXIAL_FIRST)
     assert st == ss.SSOCT_EUNSUPPORTED
     lam256 = np.linspace(800e-9, 850e-9, 256)
     st, h = ss.ssoct_create_plan(64, 64, 256, 20e-6, 0.3, lam256,
@@ -160,9 +163,10 @@ def test_binding_refuses_without_gpu(ss):
 
 
 def test_mixed_radix_plan_sizes(ss):
-    """Frame sizes outside the persistent kernel's list take the two-pass lateral
-    path (its frame buffer shows in the workspace); sweep lengths 96, 160, 200
-    are compiled; other lengths and sizes are refused."""
+    """Square frames of 384, 640 and 768 run on the persistent lateral kernel;
+    other mixed-radix sizes take the two-pass lateral path (its frame buffer
+    shows in the workspace); sweep lengths 96, 160, 200 are compiled; other
+    lengths and sizes are refused."""
     def ws(nx, ny, nl):
         lam = np.linspace(800e-9, 850e-9, nl)
         st, h = ss.ssoct_create_plan(nx, ny, nl, 20e-6, 0.3, lam)
@@ -177,10 +181,13 @@ def test_mixed_radix_plan_sizes(ss):
     for nx, ny, nl in [(100, 64, 32), (384, 384, 100), (1280, 1280, 32), (256, 256, 48)]:
         st, _ = ws(nx, ny, nl)
         assert st == ss.SSOCT_EUNSUPPORTED, (nx, ny, nl)
-    # generic plan: no scratch ring, a frame buffer [nl][ny][nx] and a chirp table instead
-    _, b_gen = ws(384, 384, 32)
-    frames = 32 * 384 * 384
-    assert b_gen >= frames * 2 + frames * 8 + 384 * 384 * 8
+    # two-pass plan: no scratch ring, a frame buffer [nl][ny][nx] and a chirp table instead
+    _, b_gen = ws(640, 384, 32)
+    frames = 32 * 640 * 384
+    assert b_gen >= frames * 2 + frames * 8 + 640 * 384 * 8
+    # the persistent kernel's plan of the same sweep holds no frame buffer
+    _, b_sq = ws(384, 384, 32)
+    assert b_sq < 32 * 384 * 384 * (2 + 8 + 8)
 
 
 def test_batch_and_autotune_refuse_without_workspace(ss):

@@ -32,7 +32,8 @@ def _dev(frames):
     return torch.from_numpy(np.ascontiguousarray(frames).view(np.int16)).cuda()
 
 
-SHAPES = [(64, 64, 32), (128, 128, 16), (384, 384, 96), (256, 256, 64), (128, 64, 200)]
+# (640, 384) takes the two-pass lateral path, the others the persistent kernel
+SHAPES = [(64, 64, 32), (128, 128, 16), (384, 384, 96), (640, 384, 32), (256, 256, 64), (128, 64, 200)]
 
 
 def test_batch_equals_separate_reconstructs(ss):
@@ -95,7 +96,7 @@ def test_autotune_choice_and_cache(ss, tmp_path):
     assert (again["lag"], again["ring_slots"], again["tc_axial"], again["axial_first"]) == \
         (r["lag"], r["ring_slots"], r["tc_axial"], r["axial_first"])
     # a generic-path plan has no lateral schedule to tune; 96 frames have no tensor-core form
-    g = synth.workload("custom", nx=384, ny=384, nlambda=96, kind="points", seed=22)
+    g = synth.workload("custom", nx=640, ny=384, nlambda=96, kind="points", seed=22)
     gp = ss.Plan(g.nx, g.ny, g.nlambda, g.pitch, g.z, g.lambdas)
     rg = gp.autotune(_dev(g.frames), cache)
     assert rg["candidates"] == 1 and rg["tc_axial"] == 0
