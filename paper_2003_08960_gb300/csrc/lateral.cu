@@ -128,19 +128,6 @@ __device__ __forceinline__ float u16_to_f(unsigned short u) {
   return __uint2float_rn((unsigned)u);
 }
 
-// Stage 2 of a transform of length N = N1 x N2: N2 N1-point DFTs spread over
-// the transform's N1 threads, NI per thread; where N1 does not divide N2
-// (384 = 16 x 24, 640 = 32 x 20, 768 = 32 x 24) the last one is idle in the
-// threads j1 >= N2 - N1 (NI - 1).  A is the register array length.
-template <int N>
-struct Stage2 {
-  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  static constexpr int NI = (N2 + N1 - 1) / N1;
-  static constexpr int A = NI * N1 > N2 ? NI * N1 : N2;
-  // stage-2 DFT i of thread j1 exists (always, for the iterations N1 fills)
-  __device__ __forceinline__ static bool live(int i, int j1) { return (i + 1) * N1 <= N2 || j1 + N1 * i < N2; }
-};
-
 // Row item: rows [item*RPI, item*RPI + RPI) of frame d.f.  The stage buffer holds
 // input rows jlo .. jlo + nrows - 1 (uint16) and the taps (in axial-first
 // order the RPI plane rows); it then serves as the transpose block.

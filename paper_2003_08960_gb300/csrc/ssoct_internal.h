@@ -21,6 +21,20 @@ __host__ __device__ constexpr int split_n1(int n) {
        : n == 256 ? 16 : n == 384 ? 16 : n == 512 ? 16 : n == 640 ? 32 : n == 768 ? 32 : n == 1024 ? 32 : 0;
 }
 
+// Stage 2 of a transform of length N = N1 x N2 (N1 = split_n1(N)) in the
+// persistent lateral kernel: N2 N1-point DFTs spread over the transform's N1
+// threads, NI per thread; where N1 does not divide N2 (384 = 16 x 24,
+// 640 = 32 x 20, 768 = 32 x 24) the last one is idle in the threads
+// j1 >= N2 - N1 (NI - 1).  A is the register array length.
+template <int N>
+struct Stage2 {
+  static constexpr int N1 = split_n1(N), N2 = N / split_n1(N);
+  static constexpr int NI = (N2 + N1 - 1) / N1;
+  static constexpr int A = NI * N1 > N2 ? NI * N1 : N2;
+  // stage-2 DFT i of thread j1 exists (always, for the iterations N1 fills)
+  __host__ __device__ static constexpr bool live(int i, int j1) { return (i + 1) * N1 <= N2 || j1 + N1 * i < N2; }
+};
+
 // Rows per tensor copy of a lateral column band: the largest divisor of ny up
 // to 256 (a box dimension's limit), so that whole boxes cover the column.
 __host__ __device__ constexpr int band_box_rows(int ny) {
