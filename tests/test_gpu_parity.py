@@ -375,6 +375,19 @@ def test_axial_first_matches_oracle(ss, shape, window):
     print(f"axial-first {shape} window={window}: complex rel L2 {err:.3e}")
 
 
+@pytest.mark.parametrize("shape,window", [((384, 384, 64), None), ((640, 640, 32), (100, 60, 400, 300)),
+                                          ((768, 768, 128), None)])
+def test_axial_first_mixed_radix(ss, shape, window):
+    """Axial-first order on the persistent kernel's mixed-radix frames (stage 2
+    with idle threads in the depth-bin epilogue): the tiled first pass (64 and
+    128 frames) and the one-tile-per-CTA pass (32 frames), against the oracle."""
+    nx, ny, nl = shape
+    w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=nx + nl + 5)
+    plan, vol, cplx, ref = _run(ss, w, window=window, method="fft", flags=ss.SSOCT_FLAG_AXIAL_FIRST)
+    err = _check(vol, cplx, ref, quadrant=window is None)
+    print(f"axial-first {shape} window={window}: complex rel L2 {err:.3e}")
+
+
 @pytest.mark.parametrize("shape,window", [((64, 64, 64), None), ((128, 64, 128), (5, 9, 101, 50))])
 def test_axial_first_decreasing_sweep(ss, shape, window):
     """A sweep from long to short wavelengths: every frame is rescaled by a ratio
