@@ -301,8 +301,8 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(co
 
 // ---------------------------------------------------------------- axial-first pass, tiled form
 //
-// Same output as rescale_axial_kernel for sweeps of 64, 128 and 256 frames, with
-// the frames read once and the real input used twice over:
+// Same output as rescale_axial_kernel for sweeps of 64, 96, 128, 160, 200 and
+// 256 frames, with the frames read once and the real input used twice over:
 //  * a tile is 64 consecutive pixels of one sensor row (a 64-pixel strip x one
 //    row), tiles numbered row by row, so that the CTAs running together cover
 //    neighbouring strips of neighbouring rows and share in L2 the source lines
@@ -323,15 +323,17 @@ __global__ void __launch_bounds__(kTile * Split<NL>::N1) rescale_axial_kernel(co
 //    pixel's taps: g = frac(u(x0)) + k (s_t - 1) in float32, column
 //    off + k + floor(g), weight g - floor(g); out-of-frame taps read the zero
 //    fill, as Eq. 5 is read here (taps outside the frame are 0).
-// The DFT over t is the axial kernel's two-stage split (N2-point DFTs in
-// registers, twiddle, exchange through shared memory, N1-point DFTs), its
-// second stage in place, so that the pair separation reads Z_{N-q} from the
-// same buffer after a barrier.
+// The DFT over t is a two-stage split N1 x N2 (ra_split_n1: the axial
+// kernel's where that gives 8 to 16 warps per tile, 16 x 6, 16 x 10 and
+// 20 x 10 for 96, 160 and 200 frames): N2-point DFTs in registers, twiddle,
+// exchange through shared memory, N1-point DFTs (idle in some threads where N1
+// does not divide N2), the second stage in place, so that the pair separation
+// reads Z_{N-q} from the same buffer after a barrier.
 struct RescaleAxialTileParams {
   int ring_start;            // gate frame t is frame (ring_start + t) mod nl of the tensor map
   const StripTap* xstrip;    // [nl][nx / 64]
   const Tap* ytab;           // [nl][ny]
-  const float2* twl;         // [N2l][N1l], sign -
+  const float2* twl;         // [N2][N1] of this pass's split (ra_split_n1), sign -
   float2* planes;            // [nl/2 + 1][ny][nx]
   const float2* cx;          // [nx] input chirp of Eq. 6 (with the centring phase)
   const float2* cy;          // [ny]
@@ -364,15 +366,17 @@ __device__ __forceinline__ float ra_sample(int k, const StripTap& xs, const Tap&
 
 template <int NL>
 struct RaTile {
-  static constexpr int N1 = Split<NL>::N1, N2 = Split<NL>::N2;
+  static constexpr int N1 = ra_split_n1(NL), N2 = NL / N1;
+  using S2 = Stage2<NL, N1>;  // stage 2: NI N1-point DFTs per thread, idle where N1 does not divide N2
   static constexpr int kThreads = 32 * N1;
   // shared memory: exchange [NL][32] complex, strip records [NL], y taps [NL],
   // twiddles [NL], then frame t's two staged rows (2 x w uint16) at t * stride,
   // then the staging mbarrier.  A tensor copy's shared-memory destination must
   // be 128-byte aligned: the staged rows start on a 128-byte boundary and each
   // frame's block is padded to a multiple of 128 bytes.
-  static constexpr size_t kStageOffset = (size_t)NL * 32 * sizeof(float2) +
-                                         (size_t)NL * (sizeof(StripTap) + sizeof(Tap) + sizeof(float2));
+  static constexpr size_t kStageOffset = ((size_t)NL * 32 * sizeof(float2) +
+                                          (size_t)NL * (sizeof(StripTap) + sizeof(Tap) + sizeof(float2)) + 127) /
+                                         128 * 128;
   static_assert(kStageOffset % 128 == 0, "staged rows on a 128-byte boundary");
   __host__ __device__ static size_t frame_stride(int w) { return ((size_t)2 * w * sizeof(uint16_t) + 127) / 128 * 128; }
   static size_t smem_bytes(int w) { return kStageOffset + (size_t)NL * frame_stride(w) + sizeof(uint64_t); }
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
                               const __grid_constant__ CUtensorMap fmap) {
   using R = RaTile<NL>;
   constexpr int N1 = R::N1, N2 = R::N2, T = R::kThreads;
-  static_assert(N2 % N1 == 0, "the second stage needs N1 | N2");
+  using S2 = typename R::S2;
   static_assert(T >= NL, "one loader thread per frame");
   // its own name: the other kernels of this file declare the dynamic shared
   // memory with 16-byte alignment, and a tensor copy needs 128 here
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
     const int y = tile / strips, strip = tile - y * strips;
     // 1. Eq. 5 samples of frames t = j1 + N1 j2 at pixels pp and pp + 32 (one
     //    complex series), N2-point DFT over j2, twiddle, exchange
-    float2 a[N2];
+    float2 a[S2::A];
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) {
       const int t = j1 + N1 * j2;
@@ -482,9 +486,10 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
     }
     // 2. N1-point DFTs, results back into the slots just read: Z_q, q = k2 + N2 k1,
     //    at row k2 N1 + k1
-    static_for<0, N2 / N1>([&](auto I) {
+    static_for<0, S2::NI>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const int k2 = j1 + N1 * i;
+      if (!S2::live(i, j1)) return;
 #pragma unroll
       for (int jj = 0; jj < N1; ++jj) a[i * N1 + jj] = ex[(k2 * N1 + jj) * 32 + pp];
       Dft<N1, -1>::template run<1, i * N1>(a);
@@ -502,9 +507,10 @@ __global__ void __launch_bounds__(RaTile<NL>::kThreads, 1)
     float2 ca = cmul(ldg2(p.cx + xa), cyv), cb = cmul(ldg2(p.cx + xa + 32), cyv);
     ca = make_float2(ca.x * h, ca.y * h);
     cb = make_float2(cb.x * h, cb.y * h);
-    static_for<0, N2 / N1>([&](auto I) {
+    static_for<0, S2::NI>([&](auto I) {
       constexpr int i = decltype(I)::value;
       const int k2 = j1 + N1 * i;
+      if (!S2::live(i, j1)) return;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
         const int q = k2 + N2 * k1;
@@ -768,12 +774,15 @@ cudaError_t launch_gate_cuts(const Plan& p, int x0, int y0, int z0, float* xy, f
 }
 
 bool rescale_axial_tiled(int nx, int nl) {
-  return nx % kRaStrip == 0 && (nl == 64 || nl == 128 || nl == 256);
+  return nx % kRaStrip == 0 && (nl == 64 || nl == 96 || nl == 128 || nl == 160 || nl == 200 || nl == 256);
 }
 
 size_t rescale_axial_tile_smem(int nl, int w) {
   if (nl == 64) return RaTile<64>::smem_bytes(w);
+  if (nl == 96) return RaTile<96>::smem_bytes(w);
   if (nl == 128) return RaTile<128>::smem_bytes(w);
+  if (nl == 160) return RaTile<160>::smem_bytes(w);
+  if (nl == 200) return RaTile<200>::smem_bytes(w);
   if (nl == 256) return RaTile<256>::smem_bytes(w);
   return 0;
 }
@@ -787,7 +796,7 @@ cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring
     tp.ring_start = ring_start;
     tp.xstrip = (const StripTap*)(p.ws + p.off_xstrip);
     tp.ytab = (const Tap*)(p.ws + p.off_ytab);
-    tp.twl = (const float2*)(p.ws + p.off_twl);
+    tp.twl = (const float2*)(p.ws + p.off_twra);
     tp.planes = planes;
     tp.cx = (const float2*)(p.ws + p.off_cx);
     tp.cy = (const float2*)(p.ws + p.off_cy);
@@ -797,7 +806,10 @@ cudaError_t launch_rescale_axial(const Plan& p, const uint16_t* frames, int ring
     tp.w = p.ra_w;
     tp.err = &((Counters*)(p.ws + p.off_ctr))->err;
     if (p.nl == 64) return launch_ra_tiles<64>(tp, fmap, p.num_sms, s);
+    if (p.nl == 96) return launch_ra_tiles<96>(tp, fmap, p.num_sms, s);
     if (p.nl == 128) return launch_ra_tiles<128>(tp, fmap, p.num_sms, s);
+    if (p.nl == 160) return launch_ra_tiles<160>(tp, fmap, p.num_sms, s);
+    if (p.nl == 200) return launch_ra_tiles<200>(tp, fmap, p.num_sms, s);
     if (p.nl == 256) return launch_ra_tiles<256>(tp, fmap, p.num_sms, s);
     return cudaErrorInvalidValue;
   }

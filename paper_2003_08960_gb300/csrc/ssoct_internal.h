@@ -26,14 +26,22 @@ __host__ __device__ constexpr int split_n1(int n) {
 // threads, NI per thread; where N1 does not divide N2 (384 = 16 x 24,
 // 640 = 32 x 20, 768 = 32 x 24) the last one is idle in the threads
 // j1 >= N2 - N1 (NI - 1).  A is the register array length.
-template <int N>
+template <int N, int N1_ = split_n1(N)>
 struct Stage2 {
-  static constexpr int N1 = split_n1(N), N2 = N / split_n1(N);
+  static constexpr int N1 = N1_, N2 = N / N1_;
   static constexpr int NI = (N2 + N1 - 1) / N1;
   static constexpr int A = NI * N1 > N2 ? NI * N1 : N2;
   // stage-2 DFT i of thread j1 exists (always, for the iterations N1 fills)
   __host__ __device__ static constexpr bool live(int i, int j1) { return (i + 1) * N1 <= N2 || j1 + N1 * i < N2; }
 };
+
+// Split of the axial-first first pass's transform over nl frames, N1 x nl/N1
+// with a tile of 32 N1 threads: the axial split where it gives 8 to 16 warps,
+// and 16 x 6, 16 x 10, 20 x 10 for 96, 160, 200 frames, whose axial splits
+// (4 x 24, 4 x 40, 5 x 40) would leave four or five warps per tile.
+__host__ __device__ constexpr int ra_split_n1(int nl) {
+  return nl == 96 ? 16 : nl == 160 ? 16 : nl == 200 ? 20 : split_n1(nl);
+}
 
 // Rows per tensor copy of a lateral column band: the largest divisor of ny up
 // to 256 (a box dimension's limit), so that whole boxes cover the column.
@@ -199,7 +207,7 @@ struct Plan {
   double alpha;             // d^2 / (lambda_1 z) = |K|
   // host tables
   std::vector<Tap> xtab, ytab;
-  std::vector<float2> cx, cy, cx2, cy2, ox, oy, twx, twy, twl;
+  std::vector<float2> cx, cy, cx2, cy2, ox, oy, twx, twy, twl, twra;
   std::vector<float2> wq;   // [nl] exp(-2 pi i k / nl), for single-bin transforms
   std::vector<unsigned short> tcb;  // SSOCT_FLAG_TC_AXIAL: BF16 hi / lo 16-point DFT matrix (operand layout)
   // SSOCT_FLAG_PUPIL: input chirp x Zernike screen, its distance z and |K|, frames per Q chunk
@@ -219,6 +227,7 @@ struct Plan {
   bool use_tc = false;       // axial pass on the tensor cores (flag, or the autotuner's choice)
   // workspace layout (byte offsets)
   size_t off_ctr, off_xtab, off_ytab, off_cx, off_cy, off_cx2, off_cy2, off_ox, off_oy, off_twx, off_twy, off_twl;
+  size_t off_twra = 0;       // twiddles of the tiled first pass's split (ra_split_n1)
   size_t off_tcb, off_wq, off_ring, off_scratch, off_inter, ws_bytes;
   size_t off_cp = 0, off_F = 0, off_Q = 0, off_red = 0;  // SSOCT_FLAG_PUPIL regions
   // Frame sizes the persistent lateral kernel does not compile (384, 640, 768)

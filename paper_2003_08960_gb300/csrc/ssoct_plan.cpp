@@ -322,6 +322,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.twx = twiddles(nx, p.n1x, p.n2x, +1);
   p.twy = twiddles(ny, p.n1y, p.n2y, +1);
   p.twl = twiddles(nlambda, p.n1l, p.n2l, -1);
+  p.twra = twiddles(nlambda, ra_split_n1(nlambda), nlambda / ra_split_n1(nlambda), -1);
   p.wq.resize(nlambda);
   for (int k = 0; k < nlambda; ++k) p.wq[k] = cis_pi(-2.0 * (double)k / nlambda);  // exp(-2 pi i k / nlambda)
   if (axial_tc_supported(nlambda)) axial_tc_table(p.tcb);  // kept for every such plan: the autotuner may switch forms
@@ -396,6 +397,7 @@ ssoct_status ssoct_create_plan(int nx, int ny, int nlambda, double pitch_m, doub
   p.off_twx = take(sizeof(float2) * p.twx.size());
   p.off_twy = take(sizeof(float2) * p.twy.size());
   p.off_twl = take(sizeof(float2) * p.twl.size());
+  p.off_twra = take(sizeof(float2) * p.twra.size());
   p.off_tcb = take(sizeof(unsigned short) * p.tcb.size());
   p.off_wq = take(sizeof(float2) * p.wq.size());
   p.off_ring = take(sizeof(uint16_t) * (size_t)nlambda * ny * nx);
@@ -473,6 +475,7 @@ ssoct_status ssoct_set_workspace(ssoct_plan h, void* dev_ptr, size_t bytes) {
       {p.off_twx, p.twx.data(), sizeof(float2) * p.twx.size()},
       {p.off_twy, p.twy.data(), sizeof(float2) * p.twy.size()},
       {p.off_twl, p.twl.data(), sizeof(float2) * p.twl.size()},
+      {p.off_twra, p.twra.data(), sizeof(float2) * p.twra.size()},
       {p.off_tcb, p.tcb.data(), sizeof(unsigned short) * p.tcb.size()},
       {p.off_wq, p.wq.data(), sizeof(float2) * p.wq.size()},
       {p.off_xstrip, p.xstrip.data(), sizeof(StripTap) * p.xstrip.size()},

@@ -375,12 +375,15 @@ def test_axial_first_matches_oracle(ss, shape, window):
     print(f"axial-first {shape} window={window}: complex rel L2 {err:.3e}")
 
 
-@pytest.mark.parametrize("shape,window", [((384, 384, 64), None), ((640, 640, 32), (100, 60, 400, 300)),
-                                          ((768, 768, 128), None)])
+@pytest.mark.parametrize("shape,window", [((384, 384, 96), None), ((640, 640, 160), (100, 60, 400, 300)),
+                                          ((768, 768, 200), None), ((384, 384, 64), None),
+                                          ((768, 768, 128), None), ((640, 640, 32), (100, 60, 400, 300))])
 def test_axial_first_mixed_radix(ss, shape, window):
     """Axial-first order on the persistent kernel's mixed-radix frames (stage 2
-    with idle threads in the depth-bin epilogue): the tiled first pass (64 and
-    128 frames) and the one-tile-per-CTA pass (32 frames), against the oracle."""
+    with idle threads in the depth-bin epilogue), with the tiled first pass on
+    its own splits of 96, 160, 200 frames (16 x 6, 16 x 10, 20 x 10, stage 2
+    with idle threads) and on 64 and 128 frames, and the one-tile-per-CTA pass
+    (32 frames), against the oracle."""
     nx, ny, nl = shape
     w = synth.workload("custom", nx=nx, ny=ny, nlambda=nl, kind="points", seed=nx + nl + 5)
     plan, vol, cplx, ref = _run(ss, w, window=window, method="fft", flags=ss.SSOCT_FLAG_AXIAL_FIRST)
