@@ -305,7 +305,8 @@ typedef struct {
  * slots (more for smaller frames, whose frames go through the queue faster),
  * times the FP32 and tensor-core axial forms when nlambda is 256, in the paper's order and, where the plan offers it, in the axial-first
  * order (Eq. 5 + Eq. 7 before Eq. 6, the same V; offered when the frame size
- * has the persistent lateral kernel, nlambda is 64, 128 or 256, the plan has no
+ * has the persistent lateral kernel and a width that is a multiple of 64,
+ * nlambda is 64, 96, 128, 160, 200 or 256, the plan has no
  * SSOCT_FLAG_PUPIL, and the half-spectrum planes fit in the sweep-axis
  * intermediate, which that order does not use).  A plan made with
  * SSOCT_FLAG_AXIAL_FIRST keeps that order.  An axial-first choice applies to
